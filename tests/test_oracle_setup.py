@@ -169,3 +169,11 @@ def test_rescale_maps_each_ball_onto_unit_interval():
     # a ball that owns its own min and max reaches 0 and 1 exactly
     sel = own == 2
     assert out[sel].min() == 0.0 and out[sel].max() == 1.0
+
+
+def test_threshold_tie_goes_to_beta():
+    """Section 3.1 sends I0 >= TH to beta: with alpha = 0, beta = 1 and
+    lambda = 1/2, TH is exactly 0.5 and a voxel of value 0.5 maps to 1."""
+    I0 = np.array([0.0, 0.5, 1.0, 0.25])[None, None, None]
+    ITH = O.threshold(I0, [(1, 0, 0, 0)], r=2.0, lam=0.5).reshape(-1)
+    np.testing.assert_array_equal(ITH, [0.0, 1.0, 1.0, 0.0])
