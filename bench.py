@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark of the 4D GSUBSURF segmentation hot path on GB300.
+
+One bench step = one whole segmentation of the medium synthetic workload
+(128x128x64 space x 32 frames = 33.5M voxels, 60 nuclei, 50 semi-implicit
+steps): set-up (thresholding, two presmoothing solves, face coefficients, u0)
+and 50 x {coefficients, red-black SOR solve to the stopping rule, rescale},
+all through the C ABI with the image already resident in HBM.
+
+metric: voxel-sweeps/s = voxels x red-black sweeps (every solve, set-up
+included) / wall time of the whole segmentation.  The roofline object is for
+the dominant kernel (the red-black half sweep): algorithmic bytes per launch /
+its CUDA-event time on the launching stream, against the measured HBM peak.
+
+--impl reference times the FP64 CPU oracle (the reference of this project) on
+a bounded crop of the same workload.  Multi-GPU (torchrun): independent
+replicas, one per GPU (the full-grid path does not shard: replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALG_BYTES_PER_VOXEL_SWEEP = 32.0   # u r/w 8 + beta/gamma 8 + 4 FP32 face weights 16
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _crop_case(case, n=(64, 64, 32, 8)):
+    import numpy as np
+    n1, n2, n3, n4 = n
+    img = case.image[:n4, :n3, :n2, :n1].copy()
+    s = case.seeds
+    keep = (s[:, 0] < n1) & (s[:, 1] < n2) & (s[:, 2] < n3) & (s[:, 3] < n4)
+    return img, s[keep]
+
+
+def oracle_sample(case, params, nsteps=1):
+    """The FP64 oracle, as it stands, on a crop of the workload: returns
+    (voxel-sweeps per second, description)."""
+    import numpy as np
+    import oracle as O
+    img, seeds = _crop_case(case)
+    P = O.OracleParams(h=tuple(params.h), tau=params.tau, eps=params.eps, K=params.K,
+                       delta=params.delta, vartheta=params.vartheta, lambda_th=params.lambda_th,
+                       r_ball=params.r_ball, R_init=params.R_init, v_init=params.v_init,
+                       sigma_t=params.sigma_t, tol=1e-12)
+    t0 = time.perf_counter()
+    u, info = O.segment(img.astype(np.float64), seeds, P, nsteps=nsteps)
+    dt = time.perf_counter() - t0
+    nv = img.size
+    sweeps = sum(info["iters"])
+    desc = (f"oracle (plain C, FP64, 1 thread) full pipeline on a {img.shape[3]}x{img.shape[2]}x"
+            f"{img.shape[1]}x{img.shape[0]} crop of the workload ({len(seeds)} seeds), {nsteps} "
+            f"step(s) solved to 1e-12; counts step-solve sweeps, times set-up too")
+    return nv * sweeps / dt, desc, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2111_11866_gb300 import synth
+    from paper_2111_11866_gb300._lib import Params
+    import oracle
+    oracle.build()
+    case = synth.medium()
+    params = Params()
+    for _ in range(args.warmup):
+        oracle_sample(case, params)
+    vals, times = [], []
+    desc = ""
+    for _ in range(args.steps):
+        v, desc, dt = oracle_sample(case, params)
+        vals.append(v)
+        times.append(dt)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": "voxel-sweeps/s", "value": value,
+            "unit": "voxel-sweeps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(case),
+            "cpu_baseline": {"value": value, "unit": "voxel-sweeps/s", "cores": 1,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "voxel-sweeps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(case):
+    n1, n2, n3, n4 = case.dims
+    return {"workload": f"medium full grid {n1}x{n2}x{n3}x{n4}, {case.meta['count']} nuclei, "
+                        f"{case.nsteps} steps", "n1": n1, "n2": n2, "n3": n3, "n4": n4,
+            "voxels": n1 * n2 * n3 * n4, "time_steps": case.nsteps,
+            "parallelism": "replicas", "l2": "inputs larger than L2 (about 3 GB resident)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_11866_gb300 import _lib, synth
+
+    case = synth.medium()
+    n1, n2, n3, n4 = case.dims
+    nvox = n1 * n2 * n3 * n4
+    params = _lib.Params.defaults()
+    stream = torch.cuda.current_stream()
+    img_d = torch.from_numpy(case.image).cuda()
+    seg = _lib.Seg4D(case.dims, stream=stream, params=params)
+
+    def one_step():
+        seg.set_image(img_d)
+        seg.set_seeds(case.seeds)
+        return seg.step(case.nsteps)
+
+    for _ in range(max(args.warmup, 0)):
+        one_step()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sweeps = 0
+    sweep_ms = 0.0
+    launches = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        info = one_step()
+        sweeps += info["sweeps_total"]
+        sweep_ms += info["sweep_ms"]
+        launches += info["launches"] + 1          # + the image split kernel of set_image
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * nvox * sweeps / (elapsed_ms / 1000.0)
+
+    # end to end through the same ABI with host buffers and copies in the timed region
+    img_h = np.ascontiguousarray(case.image)
+    out_h = np.empty_like(img_h)
+    e2e_steps = max(1, min(args.steps, 2))
+    barrier()
+    t0 = time.perf_counter()
+    e2e_sweeps = 0
+    for _ in range(e2e_steps):
+        seg.set_image(img_h)
+        seg.set_seeds(case.seeds)
+        info = seg.step(case.nsteps)
+        e2e_sweeps += info["sweeps_total"]
+        seg.read_u(out_h)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * nvox * e2e_sweeps / e2e_s
+
+    # roofline of the dominant kernel: each launch is one colour of one sweep
+    peak, peak_kind = _peaks()
+    per_launch_bytes = ALG_BYTES_PER_VOXEL_SWEEP * nvox / 2.0
+    launch_ms = sweep_ms / max(2 * sweeps, 1)
+    achieved = per_launch_bytes / (launch_ms / 1000.0) / 1e9 if launch_ms > 0 else None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc, _ = oracle_sample(case, params)
+        cpu = {"value": v, "unit": "voxel-sweeps/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": "voxel-sweeps/s", "value": value, "unit": "voxel-sweeps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(case),
+            "sweeps_per_segmentation": sweeps / args.steps,
+            "sweep_rate": nvox * sweeps / (sweep_ms / 1000.0) if sweep_ms > 0 else None,
+            "roofline": {"bound": "hbm", "kernel": "k_sweep (one colour of a red-black sweep)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "alg_bytes_per_launch": per_launch_bytes,
+                         "avg_launch_ms": launch_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "voxel-sweeps/s",
+                    "h2d_bytes_per_step": img_h.nbytes, "d2h_bytes_per_step": out_h.nbytes},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    seg.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

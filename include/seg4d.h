@@ -1,0 +1,193 @@
+/*
+ * seg4d.h -- C ABI of libseg4d, a single-GPU NVIDIA GB300 (sm_103a)
+ * implementation of the semi-implicit finite-volume scheme for the 4D
+ * generalized subjective-surface (GSUBSURF) segmentation of Uba, Mikula and
+ * Park, "4D Segmentation Algorithm with application to 3D+time Image
+ * Segmentation" (arXiv 2111.11866).
+ *
+ * Model (Section 3.1, Eq. first): u_t = |grad u| div(G0 grad u / |grad u|)
+ * on a 3D+time grid with zero Dirichlet data, G0 = g(delta |grad I_sigma^0| +
+ * vartheta |grad I_sigma^TH|), g(s) = 1/(1 + K s^2) (Eq. eg1).  Each time step
+ * solves the linear system of Eq. new1 (Eq. new for equal h) built with the
+ * reduced diamond-cell gradients of Section 3.2 and the coefficients of
+ * Eq. 111th, by red-black SOR (Eqs. 5.33, gsee and the red-black ordering of
+ * Section 3.2), and then rescales u locally (Remark, Eq. 841).
+ *
+ * Conventions shared by every entry point:
+ *  - Arrays are 4D, x fastest: index ((l*n3 + k)*n2 + j)*n1 + i for 0-based
+ *    interior voxel (i, j, k, l); l is the frame (time) axis.  This is the
+ *    4D->1D map of Section 3.7 without the ghost ring.
+ *  - The caller owns every pointer it passes.  The library copies on set and
+ *    on read and keeps no caller pointer.  `on_device` = 1 means the pointer is
+ *    device memory of the current CUDA device, 0 means host memory.
+ *  - Every call enqueues its work on the stream given to seg4d_create and
+ *    returns after that work has finished (the library synchronises the stream
+ *    where it needs a device value on the host, e.g. for the stopping test).
+ *  - Calls return a seg4d_status.  They never abort and never wait without a
+ *    bound.  After an error, seg4d_last_error() describes it.  A handle is
+ *    not thread safe: one host thread at a time per handle.
+ */
+#ifndef SEG4D_H
+#define SEG4D_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct seg4d seg4d;
+
+typedef enum {
+    SEG4D_OK = 0,
+    SEG4D_ERR_INVALID = -1,       /* bad argument: sizes, NaN/Inf parameters, NULL */
+    SEG4D_ERR_OOM = -2,           /* device allocation failed                       */
+    SEG4D_ERR_STATE = -3,         /* call out of order (e.g. step before set_image) */
+    SEG4D_ERR_NOT_CONVERGED = -4, /* a solve reached max_iters; u holds the last
+                                     iterate and the info struct is filled          */
+    SEG4D_ERR_CUDA = -5,          /* a CUDA call failed                             */
+    SEG4D_ERR_TIMEOUT = -6        /* a bounded device wait ran out                  */
+} seg4d_status;
+
+/* interior grid sizes; n4 = number of frames */
+typedef struct {
+    int n1, n2, n3, n4;
+} seg4d_dims;
+
+/* Parameters.  seg4d_default_params() fills the values used throughout
+ * Section 4 of the paper (delta = vartheta = 0.5, h = 0.01, tau = 0.01,
+ * eps = 1, sigma = h^2/8, R = 12, lambda = 0.87) plus the readings for the
+ * values the paper does not give (K = 1, v = 1, omega = 1.8, the stopping
+ * rule below). */
+typedef struct {
+    double h[4];        /* voxel sizes h1..h4 (Eq. new1)                            */
+    double tau;         /* segmentation time step                                   */
+    double eps;         /* Evans-Spruck regularisation epsilon (Eq. 3rd)            */
+    double K;           /* Perona-Malik g(s) = 1/(1 + K s^2) (Eq. eg1)              */
+    double delta;       /* weight of the presmoothed original image (Eq. first)     */
+    double vartheta;    /* weight of the presmoothed thresholded image (Eq. first)  */
+    double lambda_th;   /* TH = lambda*min + (1-lambda)*max over a ball (Sec. 3.1)  */
+    double r_ball;      /* radius (voxels) of the thresholding and rescaling balls  */
+    double R_init;      /* radius (voxels) of the initial peak (Eq. initialcond)    */
+    double v_init;      /* 1/v is the peak height of u0 (Eq. initialcond)           */
+    double sigma_t;     /* presmoothing: one implicit heat step of this length      */
+    double omega;       /* SOR relaxation of the step solves (Eq. 5.33)             */
+    double omega_smooth;/* SOR relaxation of the presmoothing solves                */
+    double tol;         /* stop when ||b - A u||_2 <= tol ||b||_2 (step solves)     */
+    double tol_smooth;  /* the same for the presmoothing solves                     */
+    int max_iters;      /* sweep cap per solve (SEG4D_ERR_NOT_CONVERGED beyond)     */
+    int check_every;    /* sweeps between two evaluations of the stopping test      */
+    int precision;      /* 0 = FP32 sweeps and coefficients (the only mode so far)  */
+    int reserved;
+} seg4d_params;
+
+/* a segmentation seed: centre c_m (voxel units, 0-based) inside frame `frame` */
+typedef struct {
+    double x, y, z;
+    int frame;
+    int reserved;
+} seg4d_seed;
+
+/* results of the last solve of a call */
+typedef struct {
+    int iters;              /* red-black sweeps of the last solve                    */
+    int status;             /* seg4d_status of the last solve                        */
+    double res_l2;          /* ||b - A u||_2 of the returned iterate                 */
+    double res_rel;         /* res_l2 / ||b||_2                                      */
+    double bnorm;           /* ||b||_2                                               */
+    double umin, umax;      /* min / max of the solved u (before rescaling)          */
+    long long sweeps_total; /* sweeps of every solve of the call (setup included)    */
+    int steps_done;         /* time steps completed by the call                      */
+    float ms;               /* device time of the call's work, milliseconds          */
+    double sweep_ms;        /* device time spent in red-black sweeps (CUDA events on
+                               the handle's stream around each batch of sweeps)      */
+    long long launches;     /* kernels the call launched                             */
+} seg4d_info;
+
+/* fields readable with seg4d_read_field; G and OFF give 8 values per voxel,
+ * face f = 2*d + (side > 0) for axis d = x1..x4, as array [voxel][8]. */
+enum {
+    SEG4D_FIELD_U = 0,        /* segmentation function u                          */
+    SEG4D_FIELD_I0 = 1,       /* the image as set                                 */
+    SEG4D_FIELD_ITH = 2,      /* locally thresholded image I^TH (Section 3.1)      */
+    SEG4D_FIELD_ISIG0 = 3,    /* presmoothed I0                                    */
+    SEG4D_FIELD_ISIGTH = 4,   /* presmoothed I^TH                                  */
+    SEG4D_FIELD_G = 5,        /* face edge coefficients G_f (Eq. 10th), 8/voxel    */
+    SEG4D_FIELD_OWNER = 6,    /* index of the seed ball a voxel follows, or -1     */
+    SEG4D_FIELD_DIAG = 7,     /* diagonal of the current step system (Eq. new1)    */
+    SEG4D_FIELD_OFF = 8       /* off-diagonal magnitudes tau*Abar*G_f/(A_f h_d^2)
+                                 of the current system, 8/voxel; faces to the
+                                 Dirichlet boundary read as 0                      */
+};
+
+/* Fill *p with the defaults described above. */
+void seg4d_default_params(seg4d_params *p);
+
+/* Allocate a handle and every device buffer for a grid of `dims` voxels on the
+ * current CUDA device.  `cuda_stream` is a cudaStream_t (NULL = the legacy
+ * default stream).  All n_d >= 1 and n1*n2*n3*n4 < 2^33.
+ * Errors: INVALID (sizes), OOM, CUDA. */
+seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out);
+
+/* Free the handle and its device memory.  NULL is accepted. */
+seg4d_status seg4d_destroy(seg4d *h);
+
+/* Copy the parameters.  Errors: INVALID (non-finite or out of range:
+ * h, tau, eps > 0; K >= 0; delta, vartheta, lambda in [0,1]; radii > 0;
+ * 0 < omega, omega_smooth < 2; tol, tol_smooth > 0; max_iters >= 1;
+ * check_every >= 1; precision 0). */
+seg4d_status seg4d_set_params(seg4d *h, const seg4d_params *p);
+
+/* Copy the 4D image I0 (n = n1*n2*n3*n4 floats).  Marks the image-derived
+ * set-up (thresholding, presmoothing, G) for recomputation.
+ * Errors: INVALID (n mismatch, NULL, non-finite values), CUDA. */
+seg4d_status seg4d_set_image(seg4d *h, const float *I0, size_t n, int on_device);
+
+/* Copy the seeds (Section 3.1, the centres C_theta).  Marks the set-up for
+ * recomputation and u for re-initialisation from u0 (Eq. initialcond)
+ * followed by a local rescale.  nseeds >= 0; a seed whose frame is outside
+ * 0..n4-1 has an empty ball.  Errors: INVALID (NaN coordinates), OOM. */
+seg4d_status seg4d_set_seed(seg4d *h, const seg4d_seed *seeds, int nseeds);
+
+/* Overwrite u (checkpoint / resume, or a chosen initial guess); cancels a
+ * pending re-initialisation from the seeds.  Errors: INVALID, CUDA. */
+seg4d_status seg4d_set_u(seg4d *h, const float *u, size_t n, int on_device);
+
+/* Run the pending set-up now: thresholding, both presmoothing solves, face
+ * coefficients G and, if pending, u0 and its rescale.  solve and step call it
+ * themselves.  Errors: STATE (no image), NOT_CONVERGED (a presmoothing solve
+ * hit max_iters), CUDA. */
+seg4d_status seg4d_setup(seg4d *h, seg4d_info *info);
+
+/* One linear solve without rescaling: build the coefficients of Eq. new1 from
+ * the current u (= u^{resc,n-1}, also the right-hand side and the initial
+ * guess) and iterate red-black SOR until the stopping rule holds.
+ * Errors: STATE, NOT_CONVERGED, CUDA.  info may be NULL. */
+seg4d_status seg4d_solve(seg4d *h, seg4d_info *info);
+
+/* nsteps time steps, each {coefficients, solve, local rescale} (Section 3.6).
+ * Stops at the first failing solve (u holds its last iterate).
+ * Errors: INVALID (nsteps < 0), STATE, NOT_CONVERGED, CUDA. */
+seg4d_status seg4d_step(seg4d *h, int nsteps, seg4d_info *info);
+
+/* Copy u out (n floats).  Errors: INVALID, CUDA. */
+seg4d_status seg4d_read_u(seg4d *h, float *dst, size_t n, int on_device);
+
+/* Copy a field out: n = n1*n2*n3*n4 floats, or 8 times that for G and OFF.
+ * Errors: INVALID (unknown field, n mismatch), STATE (field not computed yet),
+ * CUDA. */
+seg4d_status seg4d_read_field(seg4d *h, int field, float *dst, size_t n, int on_device);
+
+/* Bytes of device memory a handle of these sizes allocates. */
+size_t seg4d_device_bytes(const seg4d_dims *dims);
+
+/* Message of the last error on this handle ("" if none); valid until the next
+ * call on the handle.  h == NULL gives the message of the last failed
+ * seg4d_create. */
+const char *seg4d_last_error(const seg4d *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEG4D_H */

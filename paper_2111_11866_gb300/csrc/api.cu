@@ -1,0 +1,787 @@
+// api.cu -- host side of the C ABI declared in include/seg4d.h.
+//
+// The handle owns every device buffer (colour-split layout, see
+// seg4d_internal.cuh).  All work goes to the handle's stream; the host waits
+// on that stream only where it needs a device value (the stopping test of
+// each solve, and the end of every call).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/seg4d.h"
+#include "seg4d_internal.cuh"
+
+using namespace seg4d_impl;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct seg4d {
+    seg4d_dims dims{};
+    Layout L{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    seg4d_params p{};
+    // colour-split device arrays ([2][S] unless noted)
+    float *u = nullptr, *beta = nullptr, *gamma = nullptr, *diag = nullptr;
+    float *W = nullptr;            // [8][S] face weights by red end
+    float *G = nullptr;            // [2][8][S] face edge coefficients
+    float *I0 = nullptr, *ITH = nullptr, *Is0 = nullptr, *IsTH = nullptr;
+    int *owner = nullptr;
+    float *stage = nullptr;        // natural-layout staging, n1*n2*n3*n4 floats
+    double *partials = nullptr;    // 3 * kPartBlocks doubles (scratch)
+    double *scal = nullptr;        // 8 doubles: reduced records
+    double *host_scal = nullptr;   // pinned mirror of scal
+    SeedDev *seeds_d = nullptr;
+    SeedStat *stat_d = nullptr;
+    int nseeds = 0;
+    int seeds_cap = 0;
+    std::vector<seg4d_seed> seeds;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;    // whole call
+    cudaEvent_t evs0 = nullptr, evs1 = nullptr;  // one batch of sweeps
+    long long launches = 0;                      // kernels launched by the current call
+    double sweep_ms = 0.0;                       // sweep time of the current call
+    bool has_image = false;
+    bool setup_dirty = true;
+    bool need_u0 = false;
+    bool has_u = false;
+    bool has_coef = false;
+    std::string err;
+};
+
+namespace {
+
+seg4d_status fail(seg4d *h, seg4d_status st, const std::string &msg)
+{
+    if (h) h->err = msg;
+    return st;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(h, SEG4D_ERR_CUDA, std::string(#call " failed: ") +               \
+                                               cudaGetErrorString(e_));                   \
+    } while (0)
+
+#define CK_LAUNCH(what)                                                                   \
+    do {                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(h, SEG4D_ERR_CUDA, std::string(what " launch failed: ") +         \
+                                               cudaGetErrorString(e_));                   \
+    } while (0)
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+bool in01(double v) { return std::isfinite(v) && v >= 0.0 && v <= 1.0; }
+
+Layout make_layout(const seg4d_dims &d)
+{
+    Layout L;
+    L.n1 = d.n1;
+    L.n2 = d.n2;
+    L.n3 = d.n3;
+    L.n4 = d.n4;
+    const int half = (d.n1 + 1) / 2;
+    L.P = (half + 3) / 4 * 4;
+    L.nchunk = (L.P + 31) / 32;
+    L.njb = (d.n2 + 7) / 8;
+    L.R = d.n2 * d.n3 * d.n4;
+    L.S = (long long)L.R * L.P;
+    return L;
+}
+
+bool dims_ok(const seg4d_dims *d)
+{
+    if (!d || d->n1 < 1 || d->n2 < 1 || d->n3 < 1 || d->n4 < 1) return false;
+    if (d->n3 > 65535 || d->n4 > 65535) return false;   // grid.y / grid.z of the sweep
+    const long long rows = (long long)d->n2 * d->n3 * d->n4;
+    if (rows >= (1LL << 31)) return false;
+    const long long nv = rows * d->n1;
+    return nv < (1LL << 33);
+}
+
+size_t bytes_for(const Layout &L, long long nv)
+{
+    const size_t S = (size_t)L.S;
+    size_t b = 0;
+    b += 2 * S * sizeof(float) * 4;        // u, beta, gamma, diag
+    b += 8 * S * sizeof(float);            // W
+    b += 16 * S * sizeof(float);           // G
+    b += 2 * S * sizeof(float) * 4;        // I0, ITH, Is0, IsTH
+    b += 2 * S * sizeof(int);              // owner
+    b += (size_t)nv * sizeof(float);       // staging
+    b += 3 * kPartBlocks * sizeof(double) + 8 * sizeof(double);
+    return b;
+}
+
+long long nvox(const seg4d *h)
+{
+    return (long long)h->dims.n1 * h->dims.n2 * h->dims.n3 * h->dims.n4;
+}
+
+void free_all(seg4d *h)
+{
+    cudaFree(h->u);
+    cudaFree(h->beta);
+    cudaFree(h->gamma);
+    cudaFree(h->diag);
+    cudaFree(h->W);
+    cudaFree(h->G);
+    cudaFree(h->I0);
+    cudaFree(h->ITH);
+    cudaFree(h->Is0);
+    cudaFree(h->IsTH);
+    cudaFree(h->owner);
+    cudaFree(h->stage);
+    cudaFree(h->partials);
+    cudaFree(h->scal);
+    cudaFree(h->seeds_d);
+    cudaFree(h->stat_d);
+    if (h->host_scal) cudaFreeHost(h->host_scal);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->evs0) cudaEventDestroy(h->evs0);
+    if (h->evs1) cudaEventDestroy(h->evs1);
+}
+
+seg4d_status use_device(seg4d *h)
+{
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != h->device) CK(cudaSetDevice(h->device));
+    return SEG4D_OK;
+}
+
+// reduce the per-block records into scal[slot..slot+2]
+seg4d_status reduce_into(seg4d *h, int slot)
+{
+    launch_reduce_partials(h->partials, kPartBlocks, h->scal + slot, h->stream);
+    h->launches += 1;
+    CK_LAUNCH("reduce");
+    return SEG4D_OK;
+}
+
+seg4d_status fetch_scal(seg4d *h)
+{
+    CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return SEG4D_OK;
+}
+
+struct SolveOut {
+    int iters = 0;
+    double res = 0, bnorm = 0, umin = 0, umax = 0;
+    bool converged = false;
+};
+
+// Red-black SOR on x with the coefficients currently in beta/gamma/diag/W;
+// the per-block records of ||b||^2 must be in `partials` (written by the
+// coefficient kernel).  Stopping rule: ||b - A x||_2 <= tol ||b||_2, tested
+// before the first sweep and after every check_every sweeps.
+seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_iters,
+                          int check_every, SolveOut &out)
+{
+    const Layout &L = h->L;
+    seg4d_status st = reduce_into(h, 0);   // scal[0..2] = sum b^2, min b, max b
+    if (st) return st;
+    int it = 0;
+    bool timed_batch = false;
+    for (;;) {
+        launch_residual(L, x, h->beta, h->gamma, h->diag, h->W, h->partials, kPartBlocks,
+                        h->stream);
+        h->launches += 1;
+        CK_LAUNCH("residual");
+        if ((st = reduce_into(h, 3))) return st;   // scal[3..5] = sum r^2, min u, max u
+        if ((st = fetch_scal(h))) return st;
+        if (timed_batch) {   // the batch before this check has completed
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, h->evs0, h->evs1) == cudaSuccess) h->sweep_ms += ms;
+            timed_batch = false;
+        }
+        const double bn = std::sqrt(h->host_scal[0]);
+        const double rn = std::sqrt(h->host_scal[3]);
+        out.iters = it;
+        out.res = rn;
+        out.bnorm = bn;
+        out.umin = h->host_scal[4];
+        out.umax = h->host_scal[5];
+        if (!std::isfinite(rn))
+            return fail(h, SEG4D_ERR_NOT_CONVERGED, "residual is not finite");
+        if (rn <= tol * bn) {
+            out.converged = true;
+            return SEG4D_OK;
+        }
+        if (it >= max_iters) return SEG4D_OK;   // not converged; caller reports it
+        const int n = std::min(check_every, max_iters - it);
+        CK(cudaEventRecord(h->evs0, h->stream));
+        for (int s = 0; s < n; ++s) {
+            launch_sweep(L, 0, x, h->beta, h->gamma, h->W, (float)omega, h->stream);
+            launch_sweep(L, 1, x, h->beta, h->gamma, h->W, (float)omega, h->stream);
+        }
+        h->launches += 2LL * n;
+        CK_LAUNCH("sweep");
+        CK(cudaEventRecord(h->evs1, h->stream));
+        timed_batch = true;
+        it += n;
+    }
+}
+
+seg4d_status upload_seeds(seg4d *h)
+{
+    const int n = (int)h->seeds.size();
+    if (n > h->seeds_cap) {
+        cudaFree(h->seeds_d);
+        cudaFree(h->stat_d);
+        h->seeds_d = nullptr;
+        h->stat_d = nullptr;
+        h->seeds_cap = 0;
+        if (cudaMalloc(&h->seeds_d, sizeof(SeedDev) * n) != cudaSuccess ||
+            cudaMalloc(&h->stat_d, sizeof(SeedStat) * n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, SEG4D_ERR_OOM, "seed arrays: device allocation failed");
+        }
+        h->seeds_cap = n;
+    }
+    std::vector<SeedDev> sd(n);
+    const double rad = std::max(h->p.r_ball, h->p.R_init) + 1.0;
+    for (int m = 0; m < n; ++m) {
+        const seg4d_seed &s = h->seeds[m];
+        SeedDev &d = sd[m];
+        d.x = s.x;
+        d.y = s.y;
+        d.z = s.z;
+        d.frame = s.frame;
+        auto lo = [&](double c, int nmax) {
+            double v = std::ceil(c - rad);
+            return (int)std::max(0.0, std::min(v, (double)nmax));
+        };
+        auto hi = [&](double c, int nmax) {
+            double v = std::floor(c + rad);
+            return (int)std::min((double)(nmax - 1), std::max(v, -1.0));
+        };
+        d.bx0 = lo(s.x, h->dims.n1);
+        d.bx1 = hi(s.x, h->dims.n1);
+        d.by0 = lo(s.y, h->dims.n2);
+        d.by1 = hi(s.y, h->dims.n2);
+        d.bz0 = lo(s.z, h->dims.n3);
+        d.bz1 = hi(s.z, h->dims.n3);
+    }
+    h->nseeds = n;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(h->seeds_d, sd.data(), sizeof(SeedDev) * n, cudaMemcpyHostToDevice,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return SEG4D_OK;
+}
+
+// presmoothing of `src` into `dst` (one implicit heat step, Section 3.1)
+seg4d_status presmooth(seg4d *h, const float *src, float *dst, long long &sweeps)
+{
+    const Layout &L = h->L;
+    launch_smooth_coef(L, src, h->p.h, h->p.sigma_t, h->beta, h->gamma, h->diag, h->W,
+                       h->partials, kPartBlocks, h->stream);
+    h->launches += 1;
+    CK_LAUNCH("smooth_coef");
+    CK(cudaMemcpyAsync(dst, src, 2 * L.S * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    SolveOut so;
+    seg4d_status st = solve_system(h, dst, h->p.omega_smooth, h->p.tol_smooth, h->p.max_iters,
+                                   h->p.check_every, so);
+    if (st) return st;
+    sweeps += so.iters;
+    if (!so.converged)
+        return fail(h, SEG4D_ERR_NOT_CONVERGED, "presmoothing solve reached max_iters");
+    return SEG4D_OK;
+}
+
+seg4d_status rescale(seg4d *h)
+{
+    if (h->nseeds == 0) return SEG4D_OK;
+    launch_ball_minmax(h->L, h->seeds_d, h->nseeds, h->p.r_ball, h->u, h->stat_d, h->stream);
+    launch_rescale_apply(h->L, h->seeds_d, h->nseeds, h->p.r_ball, h->stat_d, h->owner, h->u,
+                         h->stream);
+    h->launches += 2;
+    CK_LAUNCH("rescale");
+    return SEG4D_OK;
+}
+
+seg4d_status run_setup(seg4d *h, long long &sweeps)
+{
+    if (!h->has_image) return fail(h, SEG4D_ERR_STATE, "no image set");
+    const Layout &L = h->L;
+    seg4d_status st;
+    if (h->setup_dirty) {
+        if ((st = upload_seeds(h))) return st;
+        // owners of the thresholding / rescaling balls
+        CK(cudaMemsetAsync(h->owner, 0x7F, 2 * L.S * sizeof(int), h->stream));
+        if (h->nseeds > 0) {
+            unsigned long long *dkey = nullptr;
+            if (cudaMallocAsync((void **)&dkey, 2 * L.S * sizeof(unsigned long long), h->stream) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, SEG4D_ERR_OOM, "owner distance buffer: allocation failed");
+            }
+            CK(cudaMemsetAsync(dkey, 0xFF, 2 * L.S * sizeof(unsigned long long), h->stream));
+            launch_owner(L, h->seeds_d, h->nseeds, h->p.r_ball, dkey, h->owner, h->stream);
+            h->launches += 2;
+            CK_LAUNCH("owner");
+            CK(cudaFreeAsync(dkey, h->stream));
+        }
+        // local thresholding
+        CK(cudaMemcpyAsync(h->ITH, h->I0, 2 * L.S * sizeof(float), cudaMemcpyDeviceToDevice,
+                           h->stream));
+        if (h->nseeds > 0) {
+            launch_ball_minmax(L, h->seeds_d, h->nseeds, h->p.r_ball, h->I0, h->stat_d, h->stream);
+            launch_threshold_apply(L, h->seeds_d, h->nseeds, h->p.r_ball, h->p.lambda_th,
+                                   h->stat_d, h->owner, h->I0, h->ITH, h->stream);
+            h->launches += 2;
+            CK_LAUNCH("threshold");
+        }
+        // presmoothing of both images, then the face coefficients
+        if ((st = presmooth(h, h->I0, h->Is0, sweeps))) return st;
+        if ((st = presmooth(h, h->ITH, h->IsTH, sweeps))) return st;
+        launch_face_G(L, h->Is0, h->IsTH, h->p.h, h->p.K, h->p.delta, h->p.vartheta, h->G,
+                      h->stream);
+        h->launches += 1;
+        CK_LAUNCH("face_G");
+        h->setup_dirty = false;
+        h->has_coef = false;
+    }
+    if (h->need_u0) {
+        CK(cudaMemsetAsync(h->u, 0, 2 * L.S * sizeof(float), h->stream));
+        launch_init_u(L, h->seeds_d, h->nseeds, h->p.R_init, h->p.v_init, h->u, h->stream);
+        h->launches += h->nseeds > 0 ? 1 : 0;
+        CK_LAUNCH("init_u");
+        if ((st = rescale(h))) return st;
+        h->need_u0 = false;
+        h->has_u = true;
+    }
+    if (!h->has_u) return fail(h, SEG4D_ERR_STATE, "u is not set: call set_seed or set_u");
+    return SEG4D_OK;
+}
+
+// coefficients + solve on u; fills info fields of the solve
+seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
+{
+    launch_step_coef(h->L, h->u, h->G, h->p.h, h->p.tau, h->p.eps, h->beta, h->gamma, h->diag,
+                     h->W, h->partials, kPartBlocks, h->stream);
+    h->launches += 1;
+    CK_LAUNCH("step_coef");
+    h->has_coef = true;
+    SolveOut so;
+    seg4d_status st = solve_system(h, h->u, h->p.omega, h->p.tol, h->p.max_iters,
+                                   h->p.check_every, so);
+    if (st) return st;
+    sweeps += so.iters;
+    if (info) {
+        info->iters = so.iters;
+        info->res_l2 = so.res;
+        info->bnorm = so.bnorm;
+        info->res_rel = so.bnorm > 0 ? so.res / so.bnorm : so.res;
+        info->umin = so.umin;
+        info->umax = so.umax;
+        info->status = so.converged ? SEG4D_OK : SEG4D_ERR_NOT_CONVERGED;
+    }
+    if (!so.converged)
+        return fail(h, SEG4D_ERR_NOT_CONVERGED, "step solve reached max_iters");
+    return SEG4D_OK;
+}
+
+seg4d_status copy_in(seg4d *h, const float *src, size_t n, int on_device, float *dst_split)
+{
+    if (!src) return fail(h, SEG4D_ERR_INVALID, "NULL input pointer");
+    if ((long long)n != nvox(h)) return fail(h, SEG4D_ERR_INVALID, "array size does not match dims");
+    const float *nat = src;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(h->stage, src, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        nat = h->stage;
+    }
+    launch_split_from_natural(h->L, nat, dst_split, h->stream);
+    h->launches += 1;
+    CK_LAUNCH("split");
+    return SEG4D_OK;
+}
+
+seg4d_status copy_out(seg4d *h, const float *split, float *dst, size_t n, int on_device)
+{
+    if (!dst) return fail(h, SEG4D_ERR_INVALID, "NULL output pointer");
+    if ((long long)n != nvox(h)) return fail(h, SEG4D_ERR_INVALID, "array size does not match dims");
+    float *nat = on_device ? dst : h->stage;
+    launch_natural_from_split(h->L, split, nat, h->stream);
+    h->launches += 1;
+    CK_LAUNCH("unsplit");
+    if (!on_device)
+        CK(cudaMemcpyAsync(dst, h->stage, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return SEG4D_OK;
+}
+
+struct CallTimer {
+    seg4d *h;
+    explicit CallTimer(seg4d *hh) : h(hh)
+    {
+        h->launches = 0;
+        h->sweep_ms = 0.0;
+        cudaEventRecord(h->ev0, h->stream);
+    }
+    float stop()
+    {
+        float ms = 0.0f;
+        cudaEventRecord(h->ev1, h->stream);
+        if (cudaEventSynchronize(h->ev1) == cudaSuccess) cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+        return ms;
+    }
+};
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+void seg4d_default_params(seg4d_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    for (int d = 0; d < 4; ++d) p->h[d] = 0.01;
+    p->tau = 0.01;
+    p->eps = 1.0;
+    p->K = 1.0;
+    p->delta = 0.5;
+    p->vartheta = 0.5;
+    p->lambda_th = 0.87;
+    p->r_ball = 12.0;
+    p->R_init = 12.0;
+    p->v_init = 1.0;
+    p->sigma_t = 0.01 * 0.01 / 8.0;
+    p->omega = 1.8;
+    p->omega_smooth = 1.0;
+    p->tol = 1e-5;
+    p->tol_smooth = 1e-6;
+    p->max_iters = 20000;
+    p->check_every = 10;
+    p->precision = 0;
+}
+
+size_t seg4d_device_bytes(const seg4d_dims *dims)
+{
+    if (!dims_ok(dims)) return 0;
+    Layout L = make_layout(*dims);
+    return bytes_for(L, (long long)dims->n1 * dims->n2 * dims->n3 * dims->n4);
+}
+
+seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out)
+{
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return SEG4D_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (!dims_ok(dims)) {
+        g_create_error = "invalid dims (each >= 1, n3, n4 <= 65535, n1*n2*n3*n4 < 2^33)";
+        return SEG4D_ERR_INVALID;
+    }
+    seg4d *h = new (std::nothrow) seg4d();
+    if (!h) {
+        g_create_error = "host allocation failed";
+        return SEG4D_ERR_OOM;
+    }
+    h->dims = *dims;
+    h->L = make_layout(*dims);
+    h->stream = (cudaStream_t)cuda_stream;
+    seg4d_default_params(&h->p);
+    cudaGetDevice(&h->device);
+    const Layout &L = h->L;
+    const size_t S = (size_t)L.S;
+    const long long nv = nvox(h);
+    struct A {
+        void **p;
+        size_t bytes;
+    } allocs[] = {
+        {(void **)&h->u, 2 * S * 4},     {(void **)&h->beta, 2 * S * 4},
+        {(void **)&h->gamma, 2 * S * 4}, {(void **)&h->diag, 2 * S * 4},
+        {(void **)&h->W, 8 * S * 4},     {(void **)&h->G, 16 * S * 4},
+        {(void **)&h->I0, 2 * S * 4},    {(void **)&h->ITH, 2 * S * 4},
+        {(void **)&h->Is0, 2 * S * 4},   {(void **)&h->IsTH, 2 * S * 4},
+        {(void **)&h->owner, 2 * S * 4}, {(void **)&h->stage, (size_t)nv * 4},
+        {(void **)&h->partials, 3 * kPartBlocks * sizeof(double)},
+        {(void **)&h->scal, 8 * sizeof(double)},
+    };
+    for (auto &a : allocs) {
+        if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_all(h);
+            delete h;
+            g_create_error = "device allocation failed (" + std::to_string(a.bytes) + " bytes)";
+            return SEG4D_ERR_OOM;
+        }
+        // padding slots must read as zero in every array
+        if (cudaMemsetAsync(*a.p, 0, a.bytes, h->stream) != cudaSuccess) {
+            free_all(h);
+            delete h;
+            g_create_error = "cudaMemsetAsync failed";
+            return SEG4D_ERR_CUDA;
+        }
+    }
+    if (cudaMallocHost(&h->host_scal, 8 * sizeof(double)) != cudaSuccess ||
+        cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+        cudaEventCreate(&h->evs0) != cudaSuccess || cudaEventCreate(&h->evs1) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        g_create_error = "pinned buffer / event creation failed";
+        return SEG4D_ERR_CUDA;
+    }
+    *out = h;
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_destroy(seg4d *h)
+{
+    if (!h) return SEG4D_OK;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_set_params(seg4d *h, const seg4d_params *p)
+{
+    if (!h) return SEG4D_ERR_INVALID;
+    if (!p) return fail(h, SEG4D_ERR_INVALID, "params is NULL");
+    for (int d = 0; d < 4; ++d)
+        if (!finite_pos(p->h[d])) return fail(h, SEG4D_ERR_INVALID, "h must be finite and > 0");
+    if (!finite_pos(p->tau) || !finite_pos(p->eps) || !finite_pos(p->sigma_t))
+        return fail(h, SEG4D_ERR_INVALID, "tau, eps and sigma_t must be finite and > 0");
+    if (!std::isfinite(p->K) || p->K < 0) return fail(h, SEG4D_ERR_INVALID, "K must be >= 0");
+    if (!in01(p->delta) || !in01(p->vartheta) || !in01(p->lambda_th))
+        return fail(h, SEG4D_ERR_INVALID, "delta, vartheta and lambda_th must lie in [0,1]");
+    if (!finite_pos(p->r_ball) || !finite_pos(p->R_init) || !finite_pos(p->v_init))
+        return fail(h, SEG4D_ERR_INVALID, "r_ball, R_init and v_init must be > 0");
+    if (!(p->omega > 0 && p->omega < 2) || !(p->omega_smooth > 0 && p->omega_smooth < 2))
+        return fail(h, SEG4D_ERR_INVALID, "omega and omega_smooth must lie in (0, 2)");
+    if (!finite_pos(p->tol) || !finite_pos(p->tol_smooth))
+        return fail(h, SEG4D_ERR_INVALID, "tol and tol_smooth must be finite and > 0");
+    if (p->max_iters < 1 || p->check_every < 1)
+        return fail(h, SEG4D_ERR_INVALID, "max_iters and check_every must be >= 1");
+    if (p->precision != 0) return fail(h, SEG4D_ERR_INVALID, "precision must be 0");
+    const bool geom = std::memcmp(p->h, h->p.h, sizeof(p->h)) != 0 || p->K != h->p.K ||
+                      p->delta != h->p.delta || p->vartheta != h->p.vartheta ||
+                      p->lambda_th != h->p.lambda_th || p->r_ball != h->p.r_ball ||
+                      p->sigma_t != h->p.sigma_t || p->R_init != h->p.R_init ||
+                      p->omega_smooth != h->p.omega_smooth || p->tol_smooth != h->p.tol_smooth;
+    h->p = *p;
+    if (geom) h->setup_dirty = true;
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_set_image(seg4d *h, const float *I0, size_t n, int on_device)
+{
+    if (!h) return SEG4D_ERR_INVALID;
+    seg4d_status st = use_device(h);
+    if (st) return st;
+    if (!on_device && I0 && (long long)n == nvox(h)) {
+        for (size_t v = 0; v < n; ++v)
+            if (!std::isfinite(I0[v])) return fail(h, SEG4D_ERR_INVALID, "image has NaN/Inf");
+    }
+    if ((st = copy_in(h, I0, n, on_device, h->I0))) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    h->has_image = true;
+    h->setup_dirty = true;
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_set_seed(seg4d *h, const seg4d_seed *seeds, int nseeds)
+{
+    if (!h) return SEG4D_ERR_INVALID;
+    if (nseeds < 0 || (nseeds > 0 && !seeds))
+        return fail(h, SEG4D_ERR_INVALID, "bad seed array");
+    for (int m = 0; m < nseeds; ++m)
+        if (!std::isfinite(seeds[m].x) || !std::isfinite(seeds[m].y) || !std::isfinite(seeds[m].z))
+            return fail(h, SEG4D_ERR_INVALID, "seed coordinates must be finite");
+    h->seeds.assign(seeds, seeds + nseeds);
+    h->setup_dirty = true;
+    h->need_u0 = true;
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_set_u(seg4d *h, const float *u, size_t n, int on_device)
+{
+    if (!h) return SEG4D_ERR_INVALID;
+    seg4d_status st = use_device(h);
+    if (st) return st;
+    if ((st = copy_in(h, u, n, on_device, h->u))) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    h->has_u = true;
+    h->need_u0 = false;
+    h->has_coef = false;
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_setup(seg4d *h, seg4d_info *info)
+{
+    if (!h) return SEG4D_ERR_INVALID;
+    seg4d_status st = use_device(h);
+    if (st) return st;
+    if (info) std::memset(info, 0, sizeof(*info));
+    CallTimer t(h);
+    long long sweeps = 0;
+    st = run_setup(h, sweeps);
+    const float ms = t.stop();
+    if (info) {
+        info->sweeps_total = sweeps;
+        info->ms = ms;
+        info->sweep_ms = h->sweep_ms;
+        info->launches = h->launches;
+        info->status = st;
+    }
+    return st;
+}
+
+seg4d_status seg4d_solve(seg4d *h, seg4d_info *info)
+{
+    if (!h) return SEG4D_ERR_INVALID;
+    seg4d_status st = use_device(h);
+    if (st) return st;
+    if (info) std::memset(info, 0, sizeof(*info));
+    CallTimer t(h);
+    long long sweeps = 0;
+    st = run_setup(h, sweeps);
+    if (!st) st = one_solve(h, info, sweeps);
+    const float ms = t.stop();
+    if (info) {
+        info->sweeps_total = sweeps;
+        info->ms = ms;
+        info->sweep_ms = h->sweep_ms;
+        info->launches = h->launches;
+        info->status = st;
+    }
+    return st;
+}
+
+seg4d_status seg4d_step(seg4d *h, int nsteps, seg4d_info *info)
+{
+    if (!h) return SEG4D_ERR_INVALID;
+    if (nsteps < 0) return fail(h, SEG4D_ERR_INVALID, "nsteps < 0");
+    seg4d_status st = use_device(h);
+    if (st) return st;
+    if (info) std::memset(info, 0, sizeof(*info));
+    CallTimer t(h);
+    long long sweeps = 0;
+    st = run_setup(h, sweeps);
+    int done = 0;
+    for (; !st && done < nsteps; ++done) {
+        st = one_solve(h, info, sweeps);
+        if (st) break;
+        st = rescale(h);
+    }
+    const float ms = t.stop();
+    if (info) {
+        info->sweeps_total = sweeps;
+        info->steps_done = done;
+        info->ms = ms;
+        info->sweep_ms = h->sweep_ms;
+        info->launches = h->launches;
+        info->status = st;
+    }
+    return st;
+}
+
+seg4d_status seg4d_read_u(seg4d *h, float *dst, size_t n, int on_device)
+{
+    if (!h) return SEG4D_ERR_INVALID;
+    seg4d_status st = use_device(h);
+    if (st) return st;
+    if (!h->has_u && !h->need_u0) return fail(h, SEG4D_ERR_STATE, "u is not set");
+    if (h->need_u0) {
+        long long sweeps = 0;
+        if ((st = run_setup(h, sweeps))) return st;
+    }
+    return copy_out(h, h->u, dst, n, on_device);
+}
+
+seg4d_status seg4d_read_field(seg4d *h, int field, float *dst, size_t n, int on_device)
+{
+    if (!h) return SEG4D_ERR_INVALID;
+    seg4d_status st = use_device(h);
+    if (st) return st;
+    if (!dst) return fail(h, SEG4D_ERR_INVALID, "NULL output pointer");
+    const long long nv = nvox(h);
+    switch (field) {
+    case SEG4D_FIELD_U:
+        return seg4d_read_u(h, dst, n, on_device);
+    case SEG4D_FIELD_I0:
+        if (!h->has_image) return fail(h, SEG4D_ERR_STATE, "no image set");
+        return copy_out(h, h->I0, dst, n, on_device);
+    case SEG4D_FIELD_ITH:
+    case SEG4D_FIELD_ISIG0:
+    case SEG4D_FIELD_ISIGTH:
+    case SEG4D_FIELD_OWNER:
+    case SEG4D_FIELD_G:
+        if (!h->has_image || h->setup_dirty)
+            return fail(h, SEG4D_ERR_STATE, "set-up not computed (call seg4d_setup)");
+        break;
+    case SEG4D_FIELD_DIAG:
+    case SEG4D_FIELD_OFF:
+        if (!h->has_coef) return fail(h, SEG4D_ERR_STATE, "no step coefficients computed");
+        break;
+    default:
+        return fail(h, SEG4D_ERR_INVALID, "unknown field");
+    }
+    if (field == SEG4D_FIELD_ITH) return copy_out(h, h->ITH, dst, n, on_device);
+    if (field == SEG4D_FIELD_ISIG0) return copy_out(h, h->Is0, dst, n, on_device);
+    if (field == SEG4D_FIELD_ISIGTH) return copy_out(h, h->IsTH, dst, n, on_device);
+    if (field == SEG4D_FIELD_DIAG) return copy_out(h, h->diag, dst, n, on_device);
+    if (field == SEG4D_FIELD_OWNER) {
+        if ((long long)n != nv) return fail(h, SEG4D_ERR_INVALID, "array size does not match dims");
+        float *nat = on_device ? dst : h->stage;
+        launch_owner_natural(h->L, h->owner, nat, h->stream);
+        CK_LAUNCH("owner_natural");
+        if (!on_device)
+            CK(cudaMemcpyAsync(dst, h->stage, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return SEG4D_OK;
+    }
+    // 8 values per voxel: G or OFF
+    if ((long long)n != 8 * nv)
+        return fail(h, SEG4D_ERR_INVALID, "face fields need 8 * n1*n2*n3*n4 floats");
+    float *nat8 = dst;
+    if (!on_device) {
+        if (cudaMallocAsync((void **)&nat8, n * sizeof(float), h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, SEG4D_ERR_OOM, "read_field: temporary allocation failed");
+        }
+    }
+    if (field == SEG4D_FIELD_G)
+        launch_faces_natural_from_split(h->L, h->G, nat8, h->stream);
+    else
+        launch_off_natural(h->L, h->W, h->gamma, h->diag, nat8, h->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(dst, nat8, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (!on_device) cudaFreeAsync(nat8, h->stream);
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(h, SEG4D_ERR_CUDA, std::string("read_field: ") +
+                                           cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return SEG4D_OK;
+}
+
+const char *seg4d_last_error(const seg4d *h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+}  // extern "C"

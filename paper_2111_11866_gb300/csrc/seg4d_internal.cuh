@@ -1,0 +1,134 @@
+// seg4d_internal.cuh -- device data layout and kernel launchers of libseg4d.
+//
+// Layout ("colour-split rows").  The red-black ordering of Section 3.2 colours
+// voxel (i,j,k,l) red when i+j+k+l is even.  Every array that a sweep touches
+// is stored as two half arrays, red then black.  Row r = j + n2*(k + n3*l)
+// holds the voxels of one x-line; inside a row the voxels of one colour are
+// compacted along x: voxel i sits in slot i >> 1 of its colour.  A row has
+// P = roundup(ceil(n1/2), 4) slots per colour; unused slots are padding that
+// always holds zero.  Consequences used by the kernels:
+//   - with p = (j+k+l) & 1, the red voxel of slot s is i = 2s + p and the
+//     black one is i = 2s + 1 - p;
+//   - the x-neighbours of red slot s are black slots s-1+p and s+p, those of
+//     black slot s are red slots s-p and s+1-p; the y/z/t neighbours of any
+//     slot are the other colour's same slot in rows r -+ 1, r -+ n2, r -+ n2*n3.
+// So a half sweep reads each array with unit stride (coalesced) and no lane
+// loads a value of its own colour except its own voxel.
+//
+// Face weights of the step system are stored once per face, by the face's red
+// end: every face joins one red and one black voxel, so W[f][red slot] for the
+// 8 faces f of every red voxel covers each interior face exactly once.  Faces
+// to the Dirichlet ghost ring are only needed on the diagonal, which the
+// coefficient kernel folds into D.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace seg4d_impl {
+
+struct Layout {
+    int n1, n2, n3, n4;
+    int P;          // slots per colour per row
+    int nchunk;     // ceil(P / 32): 32-slot chunks per row
+    int njb;        // ceil(n2 / 8): 8-row blocks along y
+    int R;          // rows = n2*n3*n4
+    long long S;    // slots per colour = R*P
+};
+
+// Voxel coordinates -> colour and slot (caller guarantees the voxel exists).
+__host__ __device__ inline long long slot_of(const Layout &L, int i, int j, int k, int l,
+                                             int &colour)
+{
+    int row = j + L.n2 * (k + L.n3 * l);
+    colour = (i + j + k + l) & 1;
+    return (long long)row * L.P + (i >> 1);
+}
+
+// u-like field read with zero Dirichlet ghosts (Eq. first11 with u^D = 0).
+__device__ inline float ld_dirichlet(const Layout &L, const float *__restrict__ a, int i, int j,
+                                     int k, int l)
+{
+    if ((unsigned)i >= (unsigned)L.n1 || (unsigned)j >= (unsigned)L.n2 ||
+        (unsigned)k >= (unsigned)L.n3 || (unsigned)l >= (unsigned)L.n4)
+        return 0.0f;
+    int c;
+    long long s = slot_of(L, i, j, k, l, c);
+    return a[c * L.S + s];
+}
+
+__device__ inline int clampi(int a, int n) { return a < 0 ? 0 : (a >= n ? n - 1 : a); }
+
+// image read with replicated ghosts (zero Neumann data for images).
+__device__ inline float ld_replicate(const Layout &L, const float *__restrict__ a, int i, int j,
+                                     int k, int l)
+{
+    i = clampi(i, L.n1);
+    j = clampi(j, L.n2);
+    k = clampi(k, L.n3);
+    l = clampi(l, L.n4);
+    int c;
+    long long s = slot_of(L, i, j, k, l, c);
+    return a[c * L.S + s];
+}
+
+// owner value of a voxel outside every ball (memset byte pattern 0x7F); larger
+// than any seed index, so atomicMin picks real owners over it
+constexpr int kOwnerNone = 0x7F7F7F7F;
+
+struct SeedDev {
+    double x, y, z;
+    int frame;
+    int bx0, bx1, by0, by1, bz0, bz1;   // bounding box of the ball, clipped to the grid
+};
+
+// Per-seed scalars produced on the device.
+struct SeedStat {
+    float mn, mx;     // min / max of a field over the ball
+    int count;        // voxels in the ball (0 = empty ball)
+    int pad;
+};
+
+// ---------------------------------------------------------------- launchers
+// set-up (setup_kernels.cu)
+void launch_split_from_natural(const Layout &L, const float *nat, float *split, cudaStream_t st);
+void launch_natural_from_split(const Layout &L, const float *split, float *nat, cudaStream_t st);
+void launch_faces_natural_from_split(const Layout &L, const float *split8, float *nat8,
+                                     cudaStream_t st);
+void launch_owner_natural(const Layout &L, const int *owner, float *nat, cudaStream_t st);
+void launch_off_natural(const Layout &L, const float *W, const float *gamma, const float *diag,
+                        float *nat8, cudaStream_t st);
+void launch_owner(const Layout &L, const SeedDev *seeds, int nseeds, double r,
+                  unsigned long long *dkey, int *owner, cudaStream_t st);
+void launch_ball_minmax(const Layout &L, const SeedDev *seeds, int nseeds, double r,
+                        const float *field, SeedStat *out, cudaStream_t st);
+void launch_threshold_apply(const Layout &L, const SeedDev *seeds, int nseeds, double r,
+                            double lambda, const SeedStat *stat, const int *owner,
+                            const float *I0, float *ITH, cudaStream_t st);
+void launch_init_u(const Layout &L, const SeedDev *seeds, int nseeds, double R, double v,
+                   float *u, cudaStream_t st);
+void launch_rescale_apply(const Layout &L, const SeedDev *seeds, int nseeds, double r,
+                          const SeedStat *stat, const int *owner, float *u, cudaStream_t st);
+void launch_face_G(const Layout &L, const float *Is0, const float *IsTH, const double *h,
+                   double K, double delta, double vartheta, float *G, cudaStream_t st);
+void launch_smooth_coef(const Layout &L, const float *I, const double *h, double sigma_t,
+                        float *beta, float *gamma, float *diag, float *W, double *partials,
+                        int nparts, cudaStream_t st);
+
+// step and solve (solve_kernels.cu)
+void launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,
+                      double tau, double eps, float *beta, float *gamma, float *diag, float *W,
+                      double *partials, int nparts, cudaStream_t st);
+void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,
+                  const float *W, float omega, cudaStream_t st);
+void launch_residual(const Layout &L, const float *x, const float *beta, const float *gamma,
+                     const float *diag, const float *W, double *partials, int nparts,
+                     cudaStream_t st);
+void launch_reduce_partials(const double *partials, int nparts, double *out, cudaStream_t st);
+
+// number of per-block partial records (3 doubles each: sum, min, max) the
+// reduction kernels use; the scratch array holds 3 * kPartBlocks doubles.
+constexpr int kPartBlocks = 1024;
+constexpr int kPartThreads = 256;
+
+}  // namespace seg4d_impl

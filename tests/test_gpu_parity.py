@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Bars (derived in the design doc):
+- integer and copy work is bit-exact: ball owners, the thresholded image;
+- the FP32 presmoothing solves stop at ||r|| <= 1e-6 ||b|| (the oracle at
+  1e-12): |diff| <= 2e-5 max|I|;
+- face coefficients G are FP32 functions of the presmoothed images:
+  |diff| <= 1e-3 (absolute; G in (0, 1]) -- dominated by the 1e-5 image
+  differences amplified by K|grad I|/h;
+- u after the stated steps: |diff| <= 1e-4 max|u_oracle| per voxel, and
+  identical labels (u >= 0.5) outside a one-voxel band of the oracle's level set.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2111_11866_gb300 import _lib, synth
+
+from gpu_common import REL_TOL, gpu_run, label_mismatch_outside_band, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2111_11866_gb300 import build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _small_case():
+    # odd sizes: ragged rows (n1 odd), several 32-slot chunks, 8-row blocks with a tail
+    c = synth.small_nuclei(seed=7, n=(69, 21, 13, 5), count=5, nsteps=3)
+    seeds = c.seeds.copy()
+    # seeds in several frames, one near a corner, overlapping balls
+    extra = np.array([[2, 3, 1, 2], [60, 17, 11, 4], [30, 10, 6, 1], [33, 11, 6, 1]], float)
+    return c.image, np.concatenate([seeds, extra]), c.nsteps
+
+
+@pytest.fixture(scope="module")
+def small():
+    image, seeds, nsteps = _small_case()
+    p = _lib.Params.defaults()
+    p.r_ball = 6.0
+    p.R_init = 6.0
+    gpu = gpu_run(image, seeds, nsteps, p, fields=("owner", "ITH", "Isig0", "IsigTH", "G", "u"))
+    P = oracle_params(p)
+    img = image.astype(np.float64)
+    ref = {"owner": O.owner(image.shape, seeds, P.r_ball),
+           "ITH": O.threshold(img, seeds, P.r_ball, P.lambda_th)}
+    ref["Isig0"], _ = O.presmooth(img, P.h, P.sigma_t)
+    ref["IsigTH"], _ = O.presmooth(ref["ITH"], P.h, P.sigma_t)
+    ref["G"] = O.face_G(ref["Isig0"], ref["IsigTH"], P.h, P.K, P.delta, P.vartheta)
+    ref["u0"] = O.rescale(O.init_u(image.shape, seeds, P.R_init, P.v_init), seeds, P.r_ball)
+    ref["u"], ref["info"] = O.segment(img, seeds, P, nsteps=nsteps)
+    return gpu, ref, p
+
+
+def test_owner_bit_exact(small):
+    gpu, ref, _ = small
+    np.testing.assert_array_equal(gpu["owner"].astype(np.int64), ref["owner"].astype(np.int64))
+    assert (ref["owner"] >= 0).sum() > 1000
+
+
+def test_threshold_bit_exact(small):
+    gpu, ref, _ = small
+    np.testing.assert_array_equal(gpu["ITH"], ref["ITH"].astype(np.float32))
+
+
+def test_presmoothing(small):
+    gpu, ref, _ = small
+    for name in ("Isig0", "IsigTH"):
+        scale = np.abs(ref[name]).max()
+        assert np.abs(gpu[name] - ref[name]).max() <= 2e-5 * scale, name
+
+
+def test_face_coefficients(small):
+    gpu, ref, _ = small
+    d = np.abs(gpu["G"] - ref["G"])
+    assert d.max() <= 1e-3, d.max()
+    assert (gpu["G"] > 0).all() and (gpu["G"] <= 1).all()
+
+
+def test_initial_condition(small):
+    gpu, ref, _ = small
+    np.testing.assert_allclose(gpu["u"], ref["u0"], atol=1e-6)
+
+
+def test_pipeline_small(small):
+    gpu, ref, p = small
+    u, r = gpu["u"], ref["u"]
+    err = np.abs(u - r).max()
+    assert err <= REL_TOL * np.abs(r).max(), err
+    assert label_mismatch_outside_band(u, r) == 0
+    info = gpu["info"]
+    assert info["steps_done"] == 3 and info["status"] == 0
+    assert info["res_rel"] <= p.tol
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    c = synth.tiny()
+    p = _lib.Params.defaults()
+    gpu = gpu_run(c.image, c.seeds, c.nsteps, p)
+    ref_u, ref_info = O.segment(c.image.astype(np.float64), c.seeds, oracle_params(p),
+                                nsteps=c.nsteps)
+    return gpu, ref_u, ref_info, p
+
+
+def test_pipeline_tiny_config(tiny):
+    """32x32x32x16 moving ball with a wedge gap, 10 steps."""
+    gpu, r, ref_info, p = tiny
+    u = gpu["u"]
+    err = np.abs(u - r).max()
+    assert err <= REL_TOL * np.abs(r).max(), err
+    assert label_mismatch_outside_band(u, r) == 0
+    assert gpu["info"]["steps_done"] == 10
+    # the segmentation is not trivial
+    assert (r >= 0.5).sum() > 100
+
+
+def test_solve_alone_from_given_u():
+    """The step system alone: set u, one solve (no rescale), compare with the
+    oracle's assembly + SOR from the same u and the oracle's own G."""
+    rng = np.random.default_rng(3)
+    c = synth.small_nuclei(seed=11, n=(40, 24, 18, 7), count=3, nsteps=1)
+    p = _lib.Params.defaults()
+    p.r_ball = p.R_init = 6.0
+    P = oracle_params(p)
+    u0 = np.clip(rng.normal(0.4, 0.2, size=c.image.shape), 0, 1).astype(np.float32)
+    dims = c.dims
+    with _lib.Seg4D(dims, params=p) as s:
+        s.set_image(c.image)
+        s.set_seeds(c.seeds)
+        s.setup()
+        s.set_u(u0)
+        info = s.solve()
+        ug = s.read_u()
+        off_g = s.read_field("off")
+        diag_g = s.read_field("diag")
+    img = c.image.astype(np.float64)
+    ITH = O.threshold(img, c.seeds, P.r_ball, P.lambda_th)
+    G = O.face_G(O.presmooth(img, P.h, P.sigma_t)[0], O.presmooth(ITH, P.h, P.sigma_t)[0], P.h,
+                 P.K, P.delta, P.vartheta)
+    diag, off = O.assemble(u0.astype(np.float64), G, P.h, P.tau, P.eps)
+    ur, _ = O.solve(diag, off, u0.astype(np.float64), omega=1.8, tol=1e-12)
+    np.testing.assert_allclose(diag_g, diag, rtol=2e-3)
+    # interior faces only (the ABI reports faces to the boundary as 0)
+    interior = off_g != 0
+    np.testing.assert_allclose(off_g[interior], off[interior], rtol=2e-3, atol=1e-3)
+    assert np.abs(ug - ur).max() <= REL_TOL * np.abs(ur).max()
+    assert info["res_rel"] <= p.tol
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1, 1), (1, 5, 3, 2), (7, 1, 1, 3), (2, 2, 2, 2),
+                                  (33, 9, 1, 1)])
+def test_degenerate_grids(dims):
+    rng = np.random.default_rng(sum(dims))
+    n1, n2, n3, n4 = dims
+    img = rng.uniform(size=(n4, n3, n2, n1)).astype(np.float32)
+    seeds = [((n1 - 1) / 2, (n2 - 1) / 2, (n3 - 1) / 2, 0)]
+    p = _lib.Params.defaults()
+    p.r_ball = p.R_init = 3.0
+    gpu = gpu_run(img, seeds, 2, p)
+    r, _ = O.segment(img.astype(np.float64), seeds, oracle_params(p), nsteps=2)
+    assert np.abs(gpu["u"] - r).max() <= REL_TOL * max(np.abs(r).max(), 1e-30)
+
+
+def test_no_seeds_keeps_zero():
+    img = np.random.default_rng(0).uniform(size=(3, 4, 5, 6)).astype(np.float32)
+    gpu = gpu_run(img, np.zeros((0, 4)), 2)
+    assert (gpu["u"] == 0).all()
+
+
+def test_errors_are_reported():
+    with _lib.Seg4D((8, 8, 8, 2)) as s:
+        with pytest.raises(_lib.Seg4DError) as e:
+            s.step(1)
+        assert e.value.status == _lib.ERR_STATE
+        with pytest.raises(_lib.Seg4DError) as e:
+            s.set_params(omega=2.5)
+        assert e.value.status == _lib.ERR_INVALID
+        s.set_params(omega=1.8)
+        bad = np.zeros((2, 8, 8, 8), np.float32)
+        bad[0, 0, 0, 0] = np.nan
+        with pytest.raises(_lib.Seg4DError):
+            s.set_image(bad)
+        with pytest.raises(ValueError):
+            s.set_image(np.zeros(10, np.float32))
+
+
+def test_not_converged_is_reported_and_u_kept():
+    c = synth.small_nuclei(seed=5, n=(24, 20, 12, 4), count=2, nsteps=1)
+    p = _lib.Params.defaults()
+    p.r_ball = p.R_init = 5.0
+    with _lib.Seg4D(c.dims, params=p) as s:
+        s.set_image(c.image)
+        s.set_seeds(c.seeds)
+        s.setup()
+        s.set_params(max_iters=2, check_every=1, tol=1e-12)
+        with pytest.raises(_lib.Seg4DError) as e:
+            s.solve()
+        assert e.value.status == _lib.ERR_NOT_CONVERGED
+        info = s.solve(allow_not_converged=True)
+        assert info["iters"] == 2 and info["status"] == _lib.ERR_NOT_CONVERGED
+        assert np.isfinite(s.read_u()).all()
+
+
+def test_checkpoint_resume_equals_uninterrupted():
+    c = synth.small_nuclei(seed=9, n=(30, 22, 14, 5), count=3, nsteps=4)
+    p = _lib.Params.defaults()
+    p.r_ball = p.R_init = 6.0
+    with _lib.Seg4D(c.dims, params=p) as s:
+        s.set_image(c.image)
+        s.set_seeds(c.seeds)
+        s.step(4)
+        u_all = s.read_u()
+    with _lib.Seg4D(c.dims, params=p) as s:
+        s.set_image(c.image)
+        s.set_seeds(c.seeds)
+        s.step(2)
+        ck = s.read_u()
+    with _lib.Seg4D(c.dims, params=p) as s:
+        s.set_image(c.image)
+        s.set_seeds(c.seeds)
+        s.setup()
+        s.set_u(ck)
+        s.step(2)
+        u_res = s.read_u()
+    np.testing.assert_array_equal(u_res, u_all)
+
+
+def test_device_pointers_roundtrip():
+    import torch
+    c = synth.small_nuclei(seed=3, n=(20, 16, 8, 3), count=2, nsteps=1)
+    img_d = torch.from_numpy(c.image).cuda()
+    out_d = torch.empty_like(img_d)
+    with _lib.Seg4D(c.dims, stream=torch.cuda.current_stream()) as s:
+        s.set_image(img_d)
+        s.read_field("I0", out_d)
+        torch.cuda.synchronize()
+        assert torch.equal(out_d, img_d)
+        s.set_seeds(c.seeds)
+        s.set_params(r_ball=5.0, R_init=5.0)
+        s.step(1)
+        u_host = s.read_u()
+        s.read_u(out_d)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out_d.cpu().numpy(), u_host)
