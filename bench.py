@@ -184,6 +184,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-steps", type=int, default=None,
+                    help="override the workload's 50 time steps (profiling runs only)")
     args = ap.parse_args()
 
     rank = _env_int("RANK", 0)
@@ -208,6 +210,8 @@ def main():
     from paper_2111_11866_gb300 import _lib, synth
 
     case = synth.medium()
+    if args.time_steps is not None:
+        case.nsteps = args.time_steps
     n1, n2, n3, n4 = case.dims
     nvox = n1 * n2 * n3 * n4
     params = _lib.Params.defaults()

@@ -25,7 +25,7 @@ def gpu_run(image, seeds, nsteps, params: _lib.Params | None = None, fields=()):
         s.set_image(image)
         s.set_seeds(seeds)
         setup_info = s.setup()
-        out = {name: s.read_field(name) for name in fields}
+        out = {"f_" + name: s.read_field(name) for name in fields}
         info = s.step(nsteps) if nsteps > 0 else None
         out["u"] = s.read_u()
         out["info"] = info

@@ -61,32 +61,32 @@ def small():
 
 def test_owner_bit_exact(small):
     gpu, ref, _ = small
-    np.testing.assert_array_equal(gpu["owner"].astype(np.int64), ref["owner"].astype(np.int64))
+    np.testing.assert_array_equal(gpu["f_owner"].astype(np.int64), ref["owner"].astype(np.int64))
     assert (ref["owner"] >= 0).sum() > 1000
 
 
 def test_threshold_bit_exact(small):
     gpu, ref, _ = small
-    np.testing.assert_array_equal(gpu["ITH"], ref["ITH"].astype(np.float32))
+    np.testing.assert_array_equal(gpu["f_ITH"], ref["ITH"].astype(np.float32))
 
 
 def test_presmoothing(small):
     gpu, ref, _ = small
     for name in ("Isig0", "IsigTH"):
         scale = np.abs(ref[name]).max()
-        assert np.abs(gpu[name] - ref[name]).max() <= 2e-5 * scale, name
+        assert np.abs(gpu["f_" + name] - ref[name]).max() <= 2e-5 * scale, name
 
 
 def test_face_coefficients(small):
     gpu, ref, _ = small
-    d = np.abs(gpu["G"] - ref["G"])
+    d = np.abs(gpu["f_G"] - ref["G"])
     assert d.max() <= 1e-3, d.max()
-    assert (gpu["G"] > 0).all() and (gpu["G"] <= 1).all()
+    assert (gpu["f_G"] > 0).all() and (gpu["f_G"] <= 1).all()
 
 
 def test_initial_condition(small):
     gpu, ref, _ = small
-    np.testing.assert_allclose(gpu["u"], ref["u0"], atol=1e-6)
+    np.testing.assert_allclose(gpu["f_u"], ref["u0"], atol=1e-6)
 
 
 def test_pipeline_small(small):
