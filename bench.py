@@ -32,6 +32,10 @@ sys.path.insert(0, ROOT)
 
 ALG_BYTES_PER_VOXEL_SWEEP = 32.0   # u r/w 8 + beta/gamma 8 + 4 FP32 face weights 16
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per k_sweep launch on the medium grid, from one ncu
+# capture of the current kernel (profiles/k_sweep_medium.md); None after the
+# kernel changes until it is captured again.
+SWEEP_TRAFFIC_PER_LAUNCH = 860.8e6
 
 
 def _env_int(name, default):
@@ -299,7 +303,8 @@ def main():
             "sweep_rate": nvox * sweeps / (sweep_ms / 1000.0) if sweep_ms > 0 else None,
             "roofline": {"bound": "hbm", "kernel": "k_sweep (one colour of a red-black sweep)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "frac": achieved / peak if achieved else None,
+                         "traffic": SWEEP_TRAFFIC_PER_LAUNCH,
                          "peak_kind": peak_kind,
                          "alg_bytes_per_launch": per_launch_bytes,
                          "avg_launch_ms": launch_ms},
