@@ -183,8 +183,40 @@ size_t seg4d_device_bytes(const seg4d_dims *dims);
 
 /* Message of the last error on this handle ("" if none); valid until the next
  * call on the handle.  h == NULL gives the message of the last failed
- * seg4d_create. */
+ * handle-free call of the calling thread (seg4d_create,
+ * seg4d_residual_norms_noalloc). */
 const char *seg4d_last_error(const seg4d *h);
+
+/* Residual norms of a step system that lives entirely in the caller's device
+ * memory, computed without allocating anything.  The paper has no counterpart:
+ * this is a service for callers that cannot call cudaMalloc -- for example
+ * code that hands all device memory to its own pooled allocator or fixed
+ * budget (a serving loop that admits work by HBM budget), or that must not
+ * take the device-wide synchronisation cudaMalloc/cudaFree can imply while
+ * other work is in flight.  Such callers can still check a solve.
+ *
+ * Inputs (device pointers, x-fastest arrays of n = n1*n2*n3*n4 voxels): u, b,
+ * diag (n floats each) and off (8n floats: for every voxel the magnitudes of
+ * its 8 off-diagonal entries, face f = 2*d + (side > 0), exactly as
+ * seg4d_read_field returns SEG4D_FIELD_DIAG and SEG4D_FIELD_OFF).  Faces whose
+ * neighbour lies outside the grid are ignored (zero Dirichlet data).
+ * Output: result[0] = ||b - A u||_2 and result[1] = ||b||_2, two doubles in
+ * device memory, written on `cuda_stream`; the call returns after enqueueing.
+ *
+ * Scratch: per-block FP64 records in a fixed 256 KiB device array compiled
+ * into the library, which every device that loads the library holds until the
+ * process exits.  Grids with n2*n3*n4 > 4,194,304 x-lines (or n >= 2^33) are
+ * rejected with SEG4D_ERR_INVALID.  Every call shares that array and leaves its
+ * records there; each call writes all records it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU (other streams or host threads)
+ * race on it.  The first call on a device looks up the array's device address
+ * with that device current (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  Errors: INVALID (dims, NULL, too large), CUDA; message via
+ * seg4d_last_error(NULL). */
+seg4d_status seg4d_residual_norms_noalloc(const seg4d_dims *dims, const float *u, const float *b,
+                                          const float *diag, const float *off, double *result,
+                                          void *cuda_stream);
 
 #ifdef __cplusplus
 }

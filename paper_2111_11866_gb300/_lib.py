@@ -80,7 +80,22 @@ SIGNATURES = {
     "seg4d_read_field": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.c_int]),
     "seg4d_device_bytes": (C.c_size_t, [C.POINTER(CDims)]),
     "seg4d_last_error": (C.c_char_p, [_P]),
+    "seg4d_residual_norms_noalloc": (C.c_int, [C.POINTER(CDims), _P, _P, _P, _P, _P, _P]),
 }
+
+
+def residual_norms_noalloc(dims, u, b, diag, off, result, stream=None):
+    """Binding of seg4d_residual_norms_noalloc: all arguments are CUDA tensors
+    (float32 u, b, diag of n voxels, off of 8n; float64 result of 2)."""
+    lib = load()
+    n1, n2, n3, n4 = dims
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    ptrs = [C.c_void_p(t.data_ptr()) for t in (u, b, diag, off, result)]
+    st = lib.seg4d_residual_norms_noalloc(C.byref(CDims(n1, n2, n3, n4)), *ptrs,
+                                          C.c_void_p(stream or 0))
+    if st != OK:
+        raise Seg4DError(st, lib.seg4d_last_error(None).decode())
 
 
 def load(path: str | None = None):

@@ -16,11 +16,17 @@
 
 using namespace seg4d_impl;
 
-namespace {
+namespace seg4d_impl {
+// message of the last failed handle-free call of this thread (seg4d_create,
+// seg4d_residual_norms_noalloc), reported by seg4d_last_error(NULL)
+std::string &handle_free_error()
+{
+    thread_local std::string s;
+    return s;
+}
+}  // namespace seg4d_impl
 
-thread_local std::string g_create_error;
-
-}  // namespace
+#define g_create_error handle_free_error()
 
 struct seg4d {
     seg4d_dims dims{};

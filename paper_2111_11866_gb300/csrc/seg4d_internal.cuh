@@ -23,6 +23,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace seg4d_impl {
@@ -125,6 +126,9 @@ void launch_residual(const Layout &L, const float *x, const float *beta, const f
                      const float *diag, const float *W, double *partials, int nparts,
                      cudaStream_t st);
 void launch_reduce_partials(const double *partials, int nparts, double *out, cudaStream_t st);
+
+// message of the last failed handle-free call of this thread (api.cu)
+std::string &handle_free_error();
 
 // number of per-block partial records (3 doubles each: sum, min, max) the
 // reduction kernels use; the scratch array holds 3 * kPartBlocks doubles.
