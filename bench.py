@@ -32,10 +32,12 @@ sys.path.insert(0, ROOT)
 
 ALG_BYTES_PER_VOXEL_SWEEP = 32.0   # u r/w 8 + beta/gamma 8 + 4 FP32 face weights 16
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes (read + write) per k_sweep launch on the medium grid, from one ncu
-# capture of the current kernel (profiles/k_sweep_medium.md); None after the
-# kernel changes until it is captured again.
-SWEEP_TRAFFIC_PER_LAUNCH = 860.8e6
+# DRAM bytes (read + write) per full sweep of the medium grid, from one ncu
+# capture of the current kernel (profiles/); None after a kernel changes until
+# it is captured again.
+SWEEP_KERNELS = {0: "k_sweep_wave (fused red-black wavefront, several sweeps per launch)",
+                 1: "k_sweep (one colour of a red-black sweep per launch)"}
+SWEEP_TRAFFIC_PER_SWEEP = {0: None, 1: 2 * 860.8e6}
 
 
 def _env_int(name, default):
@@ -188,6 +190,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-variant", type=int, default=1, choices=[0, 1],
+                    help="0 = fused red-black wavefront sweep, 1 = one launch per colour")
     ap.add_argument("--time-steps", type=int, default=None,
                     help="override the workload's 50 time steps (profiling runs only)")
     args = ap.parse_args()
@@ -219,6 +223,7 @@ def main():
     n1, n2, n3, n4 = case.dims
     nvox = n1 * n2 * n3 * n4
     params = _lib.Params.defaults()
+    params.sweep_variant = args.sweep_variant
     stream = torch.cuda.current_stream()
     img_d = torch.from_numpy(case.image).cuda()
     seg = _lib.Seg4D(case.dims, stream=stream, params=params)
@@ -244,11 +249,13 @@ def main():
     sweeps = 0
     sweep_ms = 0.0
     launches = 0
+    sweep_launches = 0
     e0.record(stream)
     for _ in range(args.steps):
         info = one_step()
         sweeps += info["sweeps_total"]
         sweep_ms += info["sweep_ms"]
+        sweep_launches += info["sweep_launches"]
         launches += info["launches"] + 1          # + the image split kernel of set_image
     e1.record(stream)
     barrier()
@@ -281,11 +288,14 @@ def main():
         e2e_s = float(t.item())
     e2e_value = world * nvox * e2e_sweeps / e2e_s
 
-    # roofline of the dominant kernel: each launch is one colour of one sweep
+    # roofline of the dominant kernel (the sweep): algorithmic bytes of the
+    # sweeps one launch performs / the launch's CUDA-event time
     peak, peak_kind = _peaks()
-    per_launch_bytes = ALG_BYTES_PER_VOXEL_SWEEP * nvox / 2.0
-    launch_ms = sweep_ms / max(2 * sweeps, 1)
+    sweeps_per_launch = sweeps / max(sweep_launches, 1)
+    per_launch_bytes = ALG_BYTES_PER_VOXEL_SWEEP * nvox * sweeps_per_launch
+    launch_ms = sweep_ms / max(sweep_launches, 1)
     achieved = per_launch_bytes / (launch_ms / 1000.0) / 1e9 if launch_ms > 0 else None
+    kernel_name = SWEEP_KERNELS[params.sweep_variant]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -301,12 +311,15 @@ def main():
             "config": _config(case),
             "sweeps_per_segmentation": sweeps / args.steps,
             "sweep_rate": nvox * sweeps / (sweep_ms / 1000.0) if sweep_ms > 0 else None,
-            "roofline": {"bound": "hbm", "kernel": "k_sweep (one colour of a red-black sweep)",
+            "roofline": {"bound": "hbm", "kernel": kernel_name,
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None,
-                         "traffic": SWEEP_TRAFFIC_PER_LAUNCH,
+                         "traffic": (SWEEP_TRAFFIC_PER_SWEEP[params.sweep_variant] *
+                                     sweeps_per_launch
+                                     if SWEEP_TRAFFIC_PER_SWEEP[params.sweep_variant] else None),
                          "peak_kind": peak_kind,
                          "alg_bytes_per_launch": per_launch_bytes,
+                         "sweeps_per_launch": sweeps_per_launch,
                          "avg_launch_ms": launch_ms},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "voxel-sweeps/s",

@@ -76,9 +76,19 @@ typedef struct {
     double tol;         /* stop when ||b - A u||_2 <= tol ||b||_2 (step solves)     */
     double tol_smooth;  /* the same for the presmoothing solves                     */
     int max_iters;      /* sweep cap per solve (SEG4D_ERR_NOT_CONVERGED beyond)     */
-    int check_every;    /* sweeps between two evaluations of the stopping test      */
+    int check_every;    /* sweeps before the first re-evaluation of the stopping
+                           test; later gaps are predicted from the observed
+                           residual decay, within [max(1, check_every/4),
+                           8*check_every]                                           */
     int precision;      /* 0 = FP32 sweeps and coefficients (the only mode so far)  */
-    int reserved;
+    int sweep_variant;  /* 0 = fused red-black wavefront (one pass per sweep),
+                           1 = one launch per colour (default); both give
+                           identical bits                                          */
+    int ctas_per_sm;    /* resident CTAs per SM of the fused sweep (0 = default 4)  */
+    int wait_test;      /* test hook, 0 normally.  1: the first work item of the
+                           fused sweep also waits for a flag that nothing sets,
+                           so its bounded wait expires (about 2 s) and the call
+                           returns SEG4D_ERR_TIMEOUT with u not valid            */
 } seg4d_params;
 
 /* a segmentation seed: centre c_m (voxel units, 0-based) inside frame `frame` */
@@ -102,6 +112,7 @@ typedef struct {
     double sweep_ms;        /* device time spent in red-black sweeps (CUDA events on
                                the handle's stream around each batch of sweeps)      */
     long long launches;     /* kernels the call launched                             */
+    long long sweep_launches; /* of which sweep kernels (timed by sweep_ms)          */
 } seg4d_info;
 
 /* fields readable with seg4d_read_field; G and OFF give 8 values per voxel,

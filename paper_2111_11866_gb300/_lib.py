@@ -45,7 +45,7 @@ class CParams(C.Structure):
                 ("v_init", C.c_double), ("sigma_t", C.c_double), ("omega", C.c_double),
                 ("omega_smooth", C.c_double), ("tol", C.c_double), ("tol_smooth", C.c_double),
                 ("max_iters", C.c_int), ("check_every", C.c_int), ("precision", C.c_int),
-                ("reserved", C.c_int)]
+                ("sweep_variant", C.c_int), ("ctas_per_sm", C.c_int), ("wait_test", C.c_int)]
 
 
 class CSeed(C.Structure):
@@ -57,7 +57,8 @@ class CInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("res_l2", C.c_double),
                 ("res_rel", C.c_double), ("bnorm", C.c_double), ("umin", C.c_double),
                 ("umax", C.c_double), ("sweeps_total", C.c_longlong), ("steps_done", C.c_int),
-                ("ms", C.c_float), ("sweep_ms", C.c_double), ("launches", C.c_longlong)]
+                ("ms", C.c_float), ("sweep_ms", C.c_double), ("launches", C.c_longlong),
+                ("sweep_launches", C.c_longlong)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -137,6 +138,9 @@ class Params:
     max_iters: int = 20000
     check_every: int = 10
     precision: int = 0
+    sweep_variant: int = 1
+    ctas_per_sm: int = 0
+    wait_test: int = 0
 
     @classmethod
     def defaults(cls) -> "Params":

@@ -44,6 +44,11 @@ struct seg4d {
     double *partials = nullptr;    // 3 * kPartBlocks doubles (scratch)
     double *scal = nullptr;        // 8 doubles: reduced records
     double *host_scal = nullptr;   // pinned mirror of scal
+    unsigned *wave_ctrl = nullptr; // fused-sweep control block: 4 + tiles u32
+    unsigned *host_wave = nullptr; // pinned: error flag of the last fused sweep
+    int wave_T = 0;                // tiles per frame of the fused sweep
+    int num_sms = 0;
+    int wave_occ = 1;              // occupancy limit of the fused sweep (CTAs per SM)
     SeedDev *seeds_d = nullptr;
     SeedStat *stat_d = nullptr;
     int nseeds = 0;
@@ -52,6 +57,7 @@ struct seg4d {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;    // whole call
     cudaEvent_t evs0 = nullptr, evs1 = nullptr;  // one batch of sweeps
     long long launches = 0;                      // kernels launched by the current call
+    long long sweep_launches = 0;                // of which sweep kernels
     double sweep_ms = 0.0;                       // sweep time of the current call
     bool has_image = false;
     bool setup_dirty = true;
@@ -149,6 +155,8 @@ void free_all(seg4d *h)
     cudaFree(h->stage);
     cudaFree(h->partials);
     cudaFree(h->scal);
+    cudaFree(h->wave_ctrl);
+    if (h->host_wave) cudaFreeHost(h->host_wave);
     cudaFree(h->seeds_d);
     cudaFree(h->stat_d);
     if (h->host_scal) cudaFreeHost(h->host_scal);
@@ -201,6 +209,14 @@ seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_
     if (st) return st;
     int it = 0;
     bool timed_batch = false;
+    // Checks are spaced by a prediction from the observed contraction: after
+    // two checks with r_now < r_prev, rho = (r_now/r_prev)^(1/sweeps) and the
+    // next check comes after log(tol*||b|| / r_now) / log(rho) sweeps, kept in
+    // [max(1, check_every/4), 8*check_every].  The first batch is check_every.
+    int batch = check_every;
+    double prev_rn = -1.0;
+    int prev_it = 0;
+    bool wave_pending = false;
     for (;;) {
         launch_residual(L, x, h->beta, h->gamma, h->diag, h->W, h->partials, kPartBlocks,
                         h->stream);
@@ -208,6 +224,12 @@ seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_
         CK_LAUNCH("residual");
         if ((st = reduce_into(h, 3))) return st;   // scal[3..5] = sum r^2, min u, max u
         if ((st = fetch_scal(h))) return st;
+        if (wave_pending) {
+            wave_pending = false;
+            if (h->host_wave[0] != 0u)
+                return fail(h, SEG4D_ERR_TIMEOUT,
+                            "fused sweep: a bounded wait between CTAs expired; u is not valid");
+        }
         if (timed_batch) {   // the batch before this check has completed
             float ms = 0.0f;
             if (cudaEventElapsedTime(&ms, h->evs0, h->evs1) == cudaSuccess) h->sweep_ms += ms;
@@ -227,17 +249,45 @@ seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_
             return SEG4D_OK;
         }
         if (it >= max_iters) return SEG4D_OK;   // not converged; caller reports it
-        const int n = std::min(check_every, max_iters - it);
-        CK(cudaEventRecord(h->evs0, h->stream));
-        for (int s = 0; s < n; ++s) {
-            launch_sweep(L, 0, x, h->beta, h->gamma, h->W, (float)omega, h->stream);
-            launch_sweep(L, 1, x, h->beta, h->gamma, h->W, (float)omega, h->stream);
+        if (prev_rn > 0.0 && rn < prev_rn && it > prev_it && rn > 0.0) {
+            const double rho = std::pow(rn / prev_rn, 1.0 / (it - prev_it));
+            const double need = std::log(tol * bn / rn) / std::log(rho);
+            const int lo = std::max(1, check_every / 4), hi = 8 * check_every;
+            batch = std::isfinite(need) ? (int)std::min<double>(hi, std::max<double>(lo, std::ceil(need)))
+                                        : check_every;
+        } else {
+            batch = check_every;
         }
-        h->launches += 2LL * n;
-        CK_LAUNCH("sweep");
+        prev_rn = rn;
+        prev_it = it;
+        const int n = std::min(batch, max_iters - it);
+        CK(cudaEventRecord(h->evs0, h->stream));
+        if (h->p.sweep_variant == 0) {
+            CK(cudaMemsetAsync(h->wave_ctrl, 0, (4 + h->wave_T) * sizeof(unsigned), h->stream));
+            const int per_sm = std::min(h->p.ctas_per_sm > 0 ? h->p.ctas_per_sm : 4, h->wave_occ);
+            launch_sweep_wave(L, n, x, h->beta, h->gamma, h->W, (float)omega, h->wave_ctrl,
+                              per_sm * h->num_sms, h->p.wait_test, h->stream);
+            h->launches += 1;
+            h->sweep_launches += 1;
+            CK_LAUNCH("sweep_wave");
+        } else {
+            for (int s = 0; s < n; ++s) {
+                launch_sweep(L, 0, x, h->beta, h->gamma, h->W, (float)omega, h->stream);
+                launch_sweep(L, 1, x, h->beta, h->gamma, h->W, (float)omega, h->stream);
+            }
+            h->launches += 2LL * n;
+            h->sweep_launches += 2LL * n;
+            CK_LAUNCH("sweep");
+        }
         CK(cudaEventRecord(h->evs1, h->stream));
         timed_batch = true;
         it += n;
+        if (h->p.sweep_variant == 0) {
+            // the flag is read after the next check's synchronisation
+            CK(cudaMemcpyAsync(h->host_wave, h->wave_ctrl + 2, sizeof(unsigned),
+                               cudaMemcpyDeviceToHost, h->stream));
+            wave_pending = true;
+        }
     }
 }
 
@@ -436,6 +486,7 @@ struct CallTimer {
     explicit CallTimer(seg4d *hh) : h(hh)
     {
         h->launches = 0;
+        h->sweep_launches = 0;
         h->sweep_ms = 0.0;
         cudaEventRecord(h->ev0, h->stream);
     }
@@ -475,6 +526,7 @@ void seg4d_default_params(seg4d_params *p)
     p->tol_smooth = 1e-6;
     p->max_iters = 20000;
     p->check_every = 10;
+    p->sweep_variant = 1;
     p->precision = 0;
 }
 
@@ -522,6 +574,7 @@ seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out
         {(void **)&h->owner, 2 * S * 4}, {(void **)&h->stage, (size_t)nv * 4},
         {(void **)&h->partials, 3 * kPartBlocks * sizeof(double)},
         {(void **)&h->scal, 8 * sizeof(double)},
+        {(void **)&h->wave_ctrl, (4 + (size_t)wave_tiles(L)) * sizeof(unsigned)},
     };
     for (auto &a : allocs) {
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
@@ -539,7 +592,12 @@ seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out
             return SEG4D_ERR_CUDA;
         }
     }
+    h->wave_T = wave_tiles(L);
+    h->wave_occ = wave_max_ctas_per_sm();
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (h->num_sms < 1) h->num_sms = 1;
     if (cudaMallocHost(&h->host_scal, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&h->host_wave, 4 * sizeof(unsigned)) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
         cudaEventCreate(&h->evs0) != cudaSuccess || cudaEventCreate(&h->evs1) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -582,6 +640,12 @@ seg4d_status seg4d_set_params(seg4d *h, const seg4d_params *p)
     if (p->max_iters < 1 || p->check_every < 1)
         return fail(h, SEG4D_ERR_INVALID, "max_iters and check_every must be >= 1");
     if (p->precision != 0) return fail(h, SEG4D_ERR_INVALID, "precision must be 0");
+    if (p->sweep_variant != 0 && p->sweep_variant != 1)
+        return fail(h, SEG4D_ERR_INVALID, "sweep_variant must be 0 or 1");
+    if (p->ctas_per_sm < 0 || p->ctas_per_sm > 64)
+        return fail(h, SEG4D_ERR_INVALID, "ctas_per_sm must lie in [0, 64]");
+    if (p->wait_test != 0 && p->wait_test != 1)
+        return fail(h, SEG4D_ERR_INVALID, "wait_test must be 0 or 1");
     const bool geom = std::memcmp(p->h, h->p.h, sizeof(p->h)) != 0 || p->K != h->p.K ||
                       p->delta != h->p.delta || p->vartheta != h->p.vartheta ||
                       p->lambda_th != h->p.lambda_th || p->r_ball != h->p.r_ball ||
@@ -650,6 +714,7 @@ seg4d_status seg4d_setup(seg4d *h, seg4d_info *info)
         info->ms = ms;
         info->sweep_ms = h->sweep_ms;
         info->launches = h->launches;
+        info->sweep_launches = h->sweep_launches;
         info->status = st;
     }
     return st;
@@ -671,6 +736,7 @@ seg4d_status seg4d_solve(seg4d *h, seg4d_info *info)
         info->ms = ms;
         info->sweep_ms = h->sweep_ms;
         info->launches = h->launches;
+        info->sweep_launches = h->sweep_launches;
         info->status = st;
     }
     return st;
@@ -699,6 +765,7 @@ seg4d_status seg4d_step(seg4d *h, int nsteps, seg4d_info *info)
         info->ms = ms;
         info->sweep_ms = h->sweep_ms;
         info->launches = h->launches;
+        info->sweep_launches = h->sweep_launches;
         info->status = st;
     }
     return st;

@@ -122,6 +122,11 @@ void launch_step_coef(const Layout &L, const float *u, const float *G, const dou
                       double *partials, int nparts, cudaStream_t st);
 void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,
                   const float *W, float omega, cudaStream_t st);
+void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta,
+                       const float *gamma, const float *W, float omega, unsigned *ctrl, int ctas,
+                       int test_wait, cudaStream_t st);
+int wave_tiles(const Layout &L);        // tiles per frame of the fused sweep
+int wave_max_ctas_per_sm();             // occupancy limit of the fused sweep
 void launch_residual(const Layout &L, const float *x, const float *beta, const float *gamma,
                      const float *diag, const float *W, double *partials, int nparts,
                      cudaStream_t st);
