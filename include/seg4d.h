@@ -229,6 +229,86 @@ seg4d_status seg4d_residual_norms_noalloc(const seg4d_dims *dims, const float *u
                                           const float *diag, const float *off, double *result,
                                           void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched windows.  Many independent problems (e.g. one window around each
+ * nucleus, the windows of Section 4's third and fourth experiments) advanced
+ * together: every hot kernel launch covers all active windows.  Each window
+ * runs exactly the scheme above -- set-up, then per step coefficients, red-
+ * black SOR to its own stopping rule, local rescale -- with checks of the
+ * stopping rule every check_every sweeps (no adaptive spacing), so its
+ * iterates do not depend on which other windows share the batch.
+ * ------------------------------------------------------------------------ */
+
+typedef struct seg4d_batch seg4d_batch;
+
+/* what one seg4d_batch_advance call did */
+typedef struct {
+    int setup_windows;      /* windows whose set-up ran                           */
+    int stepped_windows;    /* windows advanced by one time step                  */
+    int active_windows;     /* windows still stepping after the call (pending incl.) */
+    int done_windows;       /* windows that completed their nsteps                */
+    int failed_windows;     /* windows whose solve failed (NOT_CONVERGED / NaN)    */
+    int status;             /* seg4d_status of the call                           */
+    long long window_sweeps;/* sum over windows of the red-black sweeps run      */
+    long long launches;     /* kernels launched                                   */
+    long long arena_used;   /* bytes of the arena in use                          */
+    float ms;               /* device time of the call                            */
+    float pad;
+    double sweep_ms;        /* device time of the batched sweeps                  */
+} seg4d_batch_info;
+
+/* state of one window: 0 pending set-up, 1 active, 2 done, 3 failed */
+typedef struct {
+    int state, steps_done, nsteps, last_iters;
+    long long sweeps;       /* red-black sweeps of its step solves so far          */
+    long long device_bytes; /* arena bytes it holds                                */
+    double last_res_rel;    /* ||b - A u|| / ||b|| at the end of its last solve     */
+} seg4d_window_info;
+
+/* Create a batch with a device arena of `arena_bytes` (allocated now) for at
+ * most `max_windows` windows; work goes to `cuda_stream`.  Parameters start as
+ * seg4d_default_params().  Errors: INVALID, OOM (message via
+ * seg4d_batch_last_error(NULL)). */
+seg4d_status seg4d_batch_create(size_t arena_bytes, int max_windows, void *cuda_stream,
+                                seg4d_batch **out);
+seg4d_status seg4d_batch_destroy(seg4d_batch *b);
+
+/* Parameters shared by every window (validated as for seg4d_set_params); they
+ * apply to work done after the call. */
+seg4d_status seg4d_batch_set_params(seg4d_batch *b, const seg4d_params *p);
+
+/* Admit a window: its dims, image (copied; x fastest, host or device) and
+ * seeds (copied), and the number of time steps to run.  The window takes
+ * seg4d_batch_window_bytes(dims, nseeds) bytes of the arena (the image part
+ * is returned after its set-up).  SEG4D_ERR_OOM when the arena has no room:
+ * admission control by device-memory budget -- retry after windows are
+ * removed.  *id_out identifies the window.  Errors: INVALID, OOM, CUDA. */
+seg4d_status seg4d_batch_add(seg4d_batch *b, const seg4d_dims *dims, const float *image,
+                             int on_device, const seg4d_seed *seeds, int nseeds, int nsteps,
+                             int *id_out);
+
+/* One engine iteration: set-up of every window admitted since the last call
+ * (thresholding, presmoothing, G, u0 + rescale; Section 3.6), then one time
+ * step for every active window.  A window whose solve fails is marked failed
+ * and the others go on.  Errors: CUDA (the batch is then not usable). */
+seg4d_status seg4d_batch_advance(seg4d_batch *b, seg4d_batch_info *info);
+
+/* State of window `id`.  Errors: INVALID (unknown id). */
+seg4d_status seg4d_batch_poll(seg4d_batch *b, int id, seg4d_window_info *info);
+
+/* Copy window `id`'s u out (n = its n1*n2*n3*n4 floats, x fastest).
+ * Errors: INVALID, STATE (set-up not run yet), CUDA. */
+seg4d_status seg4d_batch_read_u(seg4d_batch *b, int id, float *dst, size_t n, int on_device);
+
+/* Retire window `id` and return its arena space.  Errors: INVALID. */
+seg4d_status seg4d_batch_remove(seg4d_batch *b, int id);
+
+/* Arena bytes a window of these sizes needs at admission. */
+size_t seg4d_batch_window_bytes(const seg4d_dims *dims, int nseeds);
+
+/* Message of the last error of the batch (NULL: of the last failed create). */
+const char *seg4d_batch_last_error(const seg4d_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

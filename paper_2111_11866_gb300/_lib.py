@@ -291,3 +291,146 @@ class Seg4D:
     def device_bytes(dims) -> int:
         n1, n2, n3, n4 = dims
         return int(load().seg4d_device_bytes(C.byref(CDims(n1, n2, n3, n4))))
+
+
+# ----------------------------------------------------------------- batches
+
+class CBatchInfo(C.Structure):
+    _fields_ = [("setup_windows", C.c_int), ("stepped_windows", C.c_int),
+                ("active_windows", C.c_int), ("done_windows", C.c_int),
+                ("failed_windows", C.c_int), ("status", C.c_int), ("window_sweeps", C.c_longlong),
+                ("launches", C.c_longlong), ("arena_used", C.c_longlong), ("ms", C.c_float),
+                ("pad", C.c_float), ("sweep_ms", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
+
+
+class CWindowInfo(C.Structure):
+    _fields_ = [("state", C.c_int), ("steps_done", C.c_int), ("nsteps", C.c_int),
+                ("last_iters", C.c_int), ("sweeps", C.c_longlong), ("device_bytes", C.c_longlong),
+                ("last_res_rel", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+SIGNATURES.update({
+    "seg4d_batch_create": (C.c_int, [C.c_size_t, C.c_int, _P, C.POINTER(_P)]),
+    "seg4d_batch_destroy": (C.c_int, [_P]),
+    "seg4d_batch_set_params": (C.c_int, [_P, C.POINTER(CParams)]),
+    "seg4d_batch_add": (C.c_int, [_P, C.POINTER(CDims), _P, C.c_int, C.POINTER(CSeed), C.c_int,
+                                  C.c_int, C.POINTER(C.c_int)]),
+    "seg4d_batch_advance": (C.c_int, [_P, C.POINTER(CBatchInfo)]),
+    "seg4d_batch_poll": (C.c_int, [_P, C.c_int, C.POINTER(CWindowInfo)]),
+    "seg4d_batch_read_u": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.c_int]),
+    "seg4d_batch_remove": (C.c_int, [_P, C.c_int]),
+    "seg4d_batch_window_bytes": (C.c_size_t, [C.POINTER(CDims), C.c_int]),
+    "seg4d_batch_last_error": (C.c_char_p, [_P]),
+})
+
+WINDOW_STATES = {0: "pending", 1: "active", 2: "done", 3: "failed"}
+
+
+def _seed_array(seeds):
+    s = np.asarray(seeds, dtype=np.float64).reshape(-1, 4)
+    arr = (CSeed * max(len(s), 1))()
+    for m, (x, y, z, f) in enumerate(s):
+        arr[m] = CSeed(float(x), float(y), float(z), int(f), 0)
+    return arr, len(s)
+
+
+class Batch:
+    """Many windows advanced together (seg4d_batch_* in seg4d.h)."""
+
+    def __init__(self, arena_bytes: int, max_windows: int = 4096, stream=None,
+                 params: Params | None = None):
+        self.lib = load()
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        h = C.c_void_p()
+        st = self.lib.seg4d_batch_create(int(arena_bytes), int(max_windows),
+                                         C.c_void_p(stream or 0), C.byref(h))
+        if st != OK:
+            raise Seg4DError(st, self.lib.seg4d_batch_last_error(None).decode())
+        self.h = h
+        self.shapes = {}
+        self.params = params or Params.defaults()
+        self.set_params(self.params)
+
+    def _check(self, st, allow=()):
+        if st != OK and st not in allow:
+            raise Seg4DError(st, self.lib.seg4d_batch_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.seg4d_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, params: Params | None = None, **kw):
+        params = params or self.params
+        for k, v in kw.items():
+            setattr(params, k, v)
+        self.params = params
+        cp = params.to_c()
+        self._check(self.lib.seg4d_batch_set_params(self.h, C.byref(cp)))
+
+    def add(self, image, seeds, nsteps: int):
+        """Admit a window; returns its id, or None when the arena has no room."""
+        if hasattr(image, "shape"):
+            n4, n3, n2, n1 = image.shape
+        else:
+            raise ValueError("image must be a 4D array (n4, n3, n2, n1)")
+        p, dev, keep = _ptr(image, n1 * n2 * n3 * n4)
+        arr, ns = _seed_array(seeds)
+        wid = C.c_int(0)
+        st = self.lib.seg4d_batch_add(self.h, C.byref(CDims(n1, n2, n3, n4)), p, dev, arr, ns,
+                                      int(nsteps), C.byref(wid))
+        if st == ERR_OOM:
+            return None
+        self._check(st)
+        self.shapes[wid.value] = (n4, n3, n2, n1)
+        return wid.value
+
+    def advance(self):
+        info = CBatchInfo()
+        self._check(self.lib.seg4d_batch_advance(self.h, C.byref(info)))
+        return info.as_dict()
+
+    def poll(self, wid: int):
+        wi = CWindowInfo()
+        self._check(self.lib.seg4d_batch_poll(self.h, int(wid), C.byref(wi)))
+        d = wi.as_dict()
+        d["state"] = WINDOW_STATES.get(d["state"], d["state"])
+        return d
+
+    def read_u(self, wid: int, out=None):
+        shape = self.shapes[wid]
+        if out is None:
+            out = np.empty(shape, dtype=np.float32)
+        n = int(np.prod(shape))
+        p, dev, keep = _ptr(out, n)
+        self._check(self.lib.seg4d_batch_read_u(self.h, int(wid), p, n, dev))
+        return out
+
+    def remove(self, wid: int):
+        self._check(self.lib.seg4d_batch_remove(self.h, int(wid)))
+        self.shapes.pop(wid, None)
+
+    @staticmethod
+    def window_bytes(dims, nseeds=1) -> int:
+        n1, n2, n3, n4 = dims
+        return int(load().seg4d_batch_window_bytes(C.byref(CDims(n1, n2, n3, n4)), int(nseeds)))

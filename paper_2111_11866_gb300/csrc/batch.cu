@@ -1,0 +1,1088 @@
+// batch.cu -- many independent segmentation windows advanced together.
+//
+// A batch owns one device arena.  Each admitted window (its own 4D grid,
+// image and seeds, e.g. a window around one nucleus) gets a contiguous block
+// of the arena for its step arrays and a second block for its images, which
+// is released once the set-up is done.  Admission fails with SEG4D_ERR_OOM
+// when the arena has no room: the byte budget is the admission control.
+//
+// One call of seg4d_batch_advance runs the set-up of every newly admitted
+// window and then one time step (coefficients, red-black SOR solve, local
+// rescale -- the same scheme as the single-grid path) for every active window.
+// The hot kernels are batched: one launch covers all windows.  A block finds
+// its window by binary search in a short table of tile offsets, then runs
+// the same per-voxel code as the single-grid kernels (stencil.cuh).
+//
+// Every window keeps its own stopping test (||b - A u||_2 <= tol ||b||_2 with
+// FP64 sums reduced per window in a fixed order) on a fixed schedule (every
+// check_every sweeps).  A window's iterates therefore depend on nothing but
+// the window itself: its result is the same, bit for bit, alone or in any
+// mix of other windows.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/seg4d.h"
+#include "stencil.cuh"
+
+namespace seg4d_impl {
+
+constexpr int kChunkTiles = 16;   // tiles per block of the reduction kernels
+
+struct BWin {
+    Layout L;
+    float *x;                      // array the current solve iterates on
+    float *u, *beta, *gamma, *diag, *W, *G;
+    int *owner;
+    SeedDev *seeds;
+    SeedStat *stat;
+    int nseeds;
+    int pad;
+};
+
+__host__ __device__ inline long long win_tiles(const Layout &L)
+{
+    return (long long)L.nchunk * L.njb * L.n3 * L.n4;
+}
+
+// largest w with starts[w] <= b (starts ascending, starts[0] = 0)
+__device__ inline int find_win(const long long *__restrict__ starts, int n, long long b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// tile t of a window -> thread's (row position, slot); false if outside
+__device__ inline bool tile_pos(const Layout &L, long long t, RowPos &rp, int &s, int &row)
+{
+    const int chunk = (int)(t % L.nchunk);
+    long long r = t / L.nchunk;
+    const int jb = (int)(r % L.njb);
+    r /= L.njb;
+    rp.k = (int)(r % L.n3);
+    rp.l = (int)(r / L.n3);
+    rp.j = jb * 8 + (int)(threadIdx.x >> 5);
+    s = chunk * 32 + (int)(threadIdx.x & 31);
+    if (rp.j >= L.n2 || s >= L.P) return false;
+    rp.p = (rp.j + rp.k + rp.l) & 1;
+    row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
+    return true;
+}
+
+// --------------------------------------------------------------- kernels
+
+template <int C>
+__global__ void __launch_bounds__(256, 8) k_bsweep(const BWin *__restrict__ wins,
+                                                   const long long *__restrict__ starts, int nwin,
+                                                   float omega)
+{
+    const long long b = blockIdx.x;
+    const int w = find_win(starts, nwin, b);
+    const Layout L = wins[w].L;
+    RowPos rp;
+    int s, row;
+    if (!tile_pos(L, b - starts[w], rp, s, row)) return;
+    if (2 * s + (C ^ rp.p) >= L.n1) return;
+    float *x = wins[w].x;
+    const float *beta = wins[w].beta, *gamma = wins[w].gamma, *W = wins[w].W;
+    const long long q = (long long)row * L.P + s;
+    const float *xo = x + (C ? 0 : L.S);
+    float *xs = x + (C ? L.S : 0);
+    const float acc = neighbour_sum<C>(L, xo, W, row, s, rp);
+    const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
+    const float u0 = xs[q];
+    xs[q] = u0 + omega * (ubar - u0);
+}
+
+// residual records per chunk of kChunkTiles tiles: (sum r^2, min x, max x)
+__global__ void __launch_bounds__(256) k_bresidual(const BWin *__restrict__ wins,
+                                                   const long long *__restrict__ cstarts, int nwin,
+                                                   double *__restrict__ parts)
+{
+    const long long b = blockIdx.x;
+    const int w = find_win(cstarts, nwin, b);
+    const Layout L = wins[w].L;
+    const float *x = wins[w].x, *beta = wins[w].beta, *gamma = wins[w].gamma;
+    const float *diag = wins[w].diag, *W = wins[w].W;
+    const long long nt = win_tiles(L);
+    const long long t0 = (b - cstarts[w]) * kChunkTiles;
+    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
+        RowPos rp;
+        int s, row;
+        if (!tile_pos(L, t, rp, s, row)) continue;
+        const long long q = (long long)row * L.P + s;
+        for (int C = 0; C < 2; ++C) {
+            if (2 * s + (C ^ rp.p) >= L.n1) continue;
+            const float acc = C ? neighbour_sum<1>(L, x, W, row, s, rp)
+                                : neighbour_sum<0>(L, x + L.S, W, row, s, rp);
+            const float u = x[C * L.S + q];
+            const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
+            const double r = (double)diag[C * L.S + q] * ((double)ubar - (double)u);
+            a.sum += r * r;
+            a.mn = fmin(a.mn, (double)u);
+            a.mx = fmax(a.mx, (double)u);
+        }
+    }
+    block_write3(a, parts + 3 * b);
+}
+
+// per-window fixed-order reduction of the chunk records (one block per window)
+__global__ void __launch_bounds__(256) k_breduce(const long long *__restrict__ cstarts,
+                                                 const double *__restrict__ parts,
+                                                 double *__restrict__ out)
+{
+    const int w = blockIdx.x;
+    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    for (long long c = cstarts[w] + threadIdx.x; c < cstarts[w + 1]; c += blockDim.x)
+        a = acc3_merge(a, Acc3{parts[3 * c], parts[3 * c + 1], parts[3 * c + 2]});
+    block_write3(a, out + 3 * w);
+}
+
+// step coefficients (Eq. new1) for every window; records (sum b^2, min, max)
+__global__ void __launch_bounds__(256) k_bcoef(const BWin *__restrict__ wins,
+                                               const long long *__restrict__ cstarts, int nwin,
+                                               StepConst K, double *__restrict__ parts)
+{
+    const long long b = blockIdx.x;
+    const int w = find_win(cstarts, nwin, b);
+    const Layout L = wins[w].L;
+    const float *u = wins[w].u, *G = wins[w].G;
+    float *beta = wins[w].beta, *gamma = wins[w].gamma, *diag = wins[w].diag, *W = wins[w].W;
+    const long long nt = win_tiles(L);
+    const long long t0 = (b - cstarts[w]) * kChunkTiles;
+    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
+        RowPos rp;
+        int s, row;
+        if (!tile_pos(L, t, rp, s, row)) continue;
+        const long long q = (long long)row * L.P + s;
+        for (int C = 0; C < 2; ++C) {
+            const int i = 2 * s + (C ^ rp.p);
+            if (i >= L.n1) continue;
+            float g2[8];
+            face_grad_sq8(L, u, i, rp.j, rp.k, rp.l, K.inv_h, g2);
+            float sum = 0.0f;
+#pragma unroll
+            for (int f = 0; f < 8; ++f) sum += g2[f];
+            const float Abar = sqrtf(K.eps2 + 0.125f * sum);
+            const float cc = K.tau * Abar;
+            float wsum = 0.0f;
+#pragma unroll
+            for (int f = 0; f < 8; ++f) {
+                const float Af = sqrtf(K.eps2 + g2[f]);
+                const float wf = G[((long long)C * 8 + f) * L.S + q] / Af * K.inv_h2[f >> 1];
+                wsum += wf;
+                if (C == 0) W[(long long)f * L.S + q] = wf;
+            }
+            const float D = 1.0f + cc * wsum;
+            const float bv = u[C * L.S + q];
+            diag[C * L.S + q] = D;
+            beta[C * L.S + q] = bv / D;
+            gamma[C * L.S + q] = cc / D;
+            a.sum += (double)bv * (double)bv;
+            a.mn = fmin(a.mn, (double)bv);
+            a.mx = fmax(a.mx, (double)bv);
+        }
+    }
+    block_write3(a, parts + 3 * b);
+}
+
+// presmoothing coefficients for every window's x (one implicit heat step,
+// zero-Neumann): w_f = 1/h_d^2 inside the grid, 0 on boundary faces
+__global__ void __launch_bounds__(256) k_bsmooth_coef(const BWin *__restrict__ wins,
+                                                      const long long *__restrict__ cstarts,
+                                                      int nwin, float4 inv_h2, float sigma_t,
+                                                      double *__restrict__ parts)
+{
+    const long long b = blockIdx.x;
+    const int w = find_win(cstarts, nwin, b);
+    const Layout L = wins[w].L;
+    const float *I = wins[w].x;
+    float *beta = wins[w].beta, *gamma = wins[w].gamma, *diag = wins[w].diag, *W = wins[w].W;
+    const float ih2[4] = {inv_h2.x, inv_h2.y, inv_h2.z, inv_h2.w};
+    const int nn[4] = {L.n1, L.n2, L.n3, L.n4};
+    const long long nt = win_tiles(L);
+    const long long t0 = (b - cstarts[w]) * kChunkTiles;
+    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
+        RowPos rp;
+        int s, row;
+        if (!tile_pos(L, t, rp, s, row)) continue;
+        const long long q = (long long)row * L.P + s;
+        for (int C = 0; C < 2; ++C) {
+            const int i = 2 * s + (C ^ rp.p);
+            if (i >= L.n1) continue;
+            const int c[4] = {i, rp.j, rp.k, rp.l};
+            float wsum = 0.0f;
+            for (int f = 0; f < 8; ++f) {
+                const int d = f >> 1;
+                const int nb = c[d] + ((f & 1) ? 1 : -1);
+                const float wf = (nb >= 0 && nb < nn[d]) ? ih2[d] : 0.0f;
+                wsum += wf;
+                if (C == 0) W[(long long)f * L.S + q] = wf;
+            }
+            const float D = 1.0f + sigma_t * wsum;
+            const float bv = I[C * L.S + q];
+            diag[C * L.S + q] = D;
+            beta[C * L.S + q] = bv / D;
+            gamma[C * L.S + q] = sigma_t / D;
+            a.sum += (double)bv * (double)bv;
+            a.mn = fmin(a.mn, (double)bv);
+            a.mx = fmax(a.mx, (double)bv);
+        }
+    }
+    block_write3(a, parts + 3 * b);
+}
+
+__device__ inline double bseed_d2(const SeedDev &sd, int i, int j, int k)
+{
+    const double dx = __dsub_rn((double)i, sd.x);
+    const double dy = __dsub_rn((double)j, sd.y);
+    const double dz = __dsub_rn((double)k, sd.z);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// per (window, seed) block: min/max of u over the ball (Eq. 841), then the
+// affine map of the owned voxels (two kernels: all min/max first)
+__global__ void __launch_bounds__(256) k_bball_minmax(const BWin *__restrict__ wins,
+                                                      const long long *__restrict__ sstarts,
+                                                      int nwin, double r2)
+{
+    const long long b = blockIdx.x;
+    const int w = find_win(sstarts, nwin, b);
+    const int m = (int)(b - sstarts[w]);
+    const Layout L = wins[w].L;
+    const SeedDev sd = wins[w].seeds[m];
+    const float *u = wins[w].u;
+    float mn = FLT_MAX, mx = -FLT_MAX;
+    int cnt = 0;
+    const int nx = sd.bx1 - sd.bx0 + 1, ny = sd.by1 - sd.by0 + 1, nz = sd.bz1 - sd.bz0 + 1;
+    const long long nb = (nx > 0 && ny > 0 && nz > 0 && sd.frame >= 0 && sd.frame < L.n4)
+                             ? (long long)nx * ny * nz
+                             : 0;
+    for (long long e = threadIdx.x; e < nb; e += blockDim.x) {
+        const int i = sd.bx0 + (int)(e % nx);
+        const int j = sd.by0 + (int)((e / nx) % ny);
+        const int k = sd.bz0 + (int)(e / ((long long)nx * ny));
+        if (bseed_d2(sd, i, j, k) <= r2) {
+            int c;
+            const long long sl = slot_of(L, i, j, k, sd.frame, c);
+            const float v = u[c * L.S + sl];
+            mn = fminf(mn, v);
+            mx = fmaxf(mx, v);
+            ++cnt;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    }
+    __shared__ float smn[8], smx[8];
+    __shared__ int scnt[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        smn[wid] = mn;
+        smx[wid] = mx;
+        scnt[wid] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            mn = fminf(mn, smn[q]);
+            mx = fmaxf(mx, smx[q]);
+            cnt += scnt[q];
+        }
+        wins[w].stat[m] = SeedStat{mn, mx, cnt, 0};
+    }
+}
+
+__global__ void __launch_bounds__(256) k_brescale_apply(const BWin *__restrict__ wins,
+                                                        const long long *__restrict__ sstarts,
+                                                        int nwin, double r2)
+{
+    const long long b = blockIdx.x;
+    const int w = find_win(sstarts, nwin, b);
+    const int m = (int)(b - sstarts[w]);
+    const Layout L = wins[w].L;
+    const SeedDev sd = wins[w].seeds[m];
+    const SeedStat ss = wins[w].stat[m];
+    if (ss.count == 0) return;
+    const double mu = ss.mn, span = (double)ss.mx - (double)ss.mn;
+    if (!(span > 1e-30)) return;
+    float *u = wins[w].u;
+    const int *owner = wins[w].owner;
+    const int nx = sd.bx1 - sd.bx0 + 1, ny = sd.by1 - sd.by0 + 1, nz = sd.bz1 - sd.bz0 + 1;
+    const long long nb = (nx > 0 && ny > 0 && nz > 0 && sd.frame >= 0 && sd.frame < L.n4)
+                             ? (long long)nx * ny * nz
+                             : 0;
+    for (long long e = threadIdx.x; e < nb; e += blockDim.x) {
+        const int i = sd.bx0 + (int)(e % nx);
+        const int j = sd.by0 + (int)((e / nx) % ny);
+        const int k = sd.bz0 + (int)(e / ((long long)nx * ny));
+        if (bseed_d2(sd, i, j, k) <= r2) {
+            int c;
+            const long long sl = slot_of(L, i, j, k, sd.frame, c);
+            if (owner[c * L.S + sl] == m)
+                u[c * L.S + sl] = (float)(((double)u[c * L.S + sl] - mu) / span);
+        }
+    }
+}
+
+}  // namespace seg4d_impl
+
+// ==================================================================== host
+
+using namespace seg4d_impl;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// first-fit allocator over the arena (offsets), with coalescing
+struct Arena {
+    char *base = nullptr;
+    size_t bytes = 0;
+    std::map<size_t, size_t> free_;   // offset -> size
+    size_t used = 0;
+
+    void init(char *b, size_t n)
+    {
+        base = b;
+        bytes = n;
+        free_.clear();
+        free_[0] = n;
+        used = 0;
+    }
+    bool alloc(size_t n, size_t &off)
+    {
+        n = align_up(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                off = it->first;
+                const size_t rest = it->second - n;
+                free_.erase(it);
+                if (rest) free_[off + n] = rest;
+                used += n;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t n)
+    {
+        n = align_up(n);
+        used -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+enum WinState { kPending = 0, kActive = 1, kDone = 2, kFailed = 3 };
+
+struct Window {
+    int id = 0;
+    seg4d_dims dims{};
+    Layout L{};
+    size_t off_main = 0, bytes_main = 0, off_img = 0, bytes_img = 0;
+    bool has_img = false;
+    BWin d{};
+    float *I0 = nullptr, *ITH = nullptr, *Is0 = nullptr, *IsTH = nullptr;
+    std::vector<seg4d_seed> seeds;
+    int nsteps = 0, steps_done = 0;
+    int state = kPending;
+    long long sweeps = 0;
+    int last_iters = 0;
+    double last_res_rel = 0.0;
+    std::string err;
+};
+
+}  // namespace
+
+struct seg4d_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    seg4d_params p{};
+    char *arena_mem = nullptr;
+    Arena arena;
+    int max_windows = 0;
+    std::map<int, Window> wins;
+    int next_id = 1;
+    // device tables (capacity max_windows) and their pinned host mirrors
+    BWin *d_wins = nullptr, *h_wins = nullptr;
+    long long *d_starts = nullptr, *h_starts = nullptr;
+    double *d_out = nullptr, *h_out = nullptr;
+    double *d_parts = nullptr;
+    size_t parts_cap = 0;    // chunk records
+    long long launches = 0;
+    double sweep_ms = 0.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+seg4d_status bfail(seg4d_batch *b, seg4d_status st, const std::string &m)
+{
+    if (b) b->err = m;
+    return st;
+}
+
+#define BCK(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return bfail(b, SEG4D_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+Layout layout_of(const seg4d_dims &d)
+{
+    Layout L;
+    L.n1 = d.n1;
+    L.n2 = d.n2;
+    L.n3 = d.n3;
+    L.n4 = d.n4;
+    L.P = ((d.n1 + 1) / 2 + 3) / 4 * 4;
+    L.nchunk = (L.P + 31) / 32;
+    L.njb = (d.n2 + 7) / 8;
+    L.R = d.n2 * d.n3 * d.n4;
+    L.S = (long long)L.R * L.P;
+    return L;
+}
+
+// main block: u, beta, gamma, diag (2S each), W (8S), G (16S) floats, owner
+// (2S ints), seeds, seed stats; image block: I0, ITH, Is0, IsTH (2S each)
+size_t main_bytes(const Layout &L, int nseeds)
+{
+    const size_t S = (size_t)L.S;
+    return align_up(32 * S * 4) + align_up(2 * S * 4) +
+           align_up(sizeof(SeedDev) * std::max(nseeds, 1)) +
+           align_up(sizeof(SeedStat) * std::max(nseeds, 1));
+}
+
+size_t img_bytes(const Layout &L) { return align_up(8 * (size_t)L.S * 4); }
+
+void carve(seg4d_batch *b, Window &w)
+{
+    const size_t S = (size_t)w.L.S;
+    char *m = b->arena.base + w.off_main;
+    float *f = (float *)m;
+    w.d.L = w.L;
+    w.d.u = f;
+    w.d.beta = f + 2 * S;
+    w.d.gamma = f + 4 * S;
+    w.d.diag = f + 6 * S;
+    w.d.W = f + 8 * S;
+    w.d.G = f + 16 * S;
+    char *p = m + align_up(32 * S * 4);
+    w.d.owner = (int *)p;
+    p += align_up(2 * S * 4);
+    w.d.seeds = (SeedDev *)p;
+    p += align_up(sizeof(SeedDev) * std::max((int)w.seeds.size(), 1));
+    w.d.stat = (SeedStat *)p;
+    w.d.nseeds = (int)w.seeds.size();
+    w.d.x = w.d.u;
+    float *g = (float *)(b->arena.base + w.off_img);
+    w.I0 = g;
+    w.ITH = g + 2 * S;
+    w.Is0 = g + 4 * S;
+    w.IsTH = g + 6 * S;
+}
+
+// chunk / tile / seed offsets of a window list into h_starts, returns total
+template <class F>
+long long fill_starts(seg4d_batch *b, const std::vector<Window *> &ws, F count)
+{
+    long long acc = 0;
+    for (size_t i = 0; i < ws.size(); ++i) {
+        b->h_starts[i] = acc;
+        acc += count(*ws[i]);
+    }
+    b->h_starts[ws.size()] = acc;
+    return acc;
+}
+
+seg4d_status upload_tables(seg4d_batch *b, const std::vector<Window *> &ws)
+{
+    for (size_t i = 0; i < ws.size(); ++i) b->h_wins[i] = ws[i]->d;
+    BCK(cudaMemcpyAsync(b->d_wins, b->h_wins, sizeof(BWin) * ws.size(), cudaMemcpyHostToDevice,
+                        b->stream));
+    return SEG4D_OK;
+}
+
+seg4d_status upload_starts(seg4d_batch *b, size_t n)
+{
+    BCK(cudaMemcpyAsync(b->d_starts, b->h_starts, sizeof(long long) * (n + 1),
+                        cudaMemcpyHostToDevice, b->stream));
+    return SEG4D_OK;
+}
+
+long long chunks_of(const Window &w) { return (win_tiles(w.L) + kChunkTiles - 1) / kChunkTiles; }
+
+seg4d_status ensure_parts(seg4d_batch *b, long long nchunks)
+{
+    if ((size_t)nchunks <= b->parts_cap) return SEG4D_OK;
+    BCK(cudaStreamSynchronize(b->stream));
+    cudaFree(b->d_parts);
+    b->d_parts = nullptr;
+    const size_t cap = (size_t)nchunks + nchunks / 4 + 1024;
+    if (cudaMalloc(&b->d_parts, 3 * sizeof(double) * cap) != cudaSuccess) {
+        cudaGetLastError();
+        b->parts_cap = 0;
+        return bfail(b, SEG4D_ERR_OOM, "batch: reduction records: allocation failed");
+    }
+    b->parts_cap = cap;
+    return SEG4D_OK;
+}
+
+// Records of a chunked kernel -> per-window (sum, min, max) in h_out.
+seg4d_status reduce_windows(seg4d_batch *b, size_t nw)
+{
+    k_breduce<<<(unsigned)nw, 256, 0, b->stream>>>(b->d_starts, b->d_parts, b->d_out);
+    b->launches += 1;
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(b->h_out, b->d_out, 3 * sizeof(double) * nw, cudaMemcpyDeviceToHost,
+                        b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return SEG4D_OK;
+}
+
+struct SolveItem {
+    Window *w;
+    double bnorm;
+    int iters;
+    bool done;
+    bool ok;
+};
+
+// Batched red-black SOR over every window of `items` (each window's d.x,
+// beta, gamma, diag, W already set up).  Per window: stop when
+// ||b - A x|| <= tol ||b||, tested every check_every sweeps.
+seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double omega, double tol,
+                         int max_iters, int check_every, long long &sweeps_total)
+{
+    std::vector<SolveItem *> act;
+    for (auto &it : items) act.push_back(&it);
+    int it = 0;
+    bool timed = false;
+    while (!act.empty()) {
+        std::vector<Window *> ws;
+        for (auto *a : act) ws.push_back(a->w);
+        seg4d_status st;
+        if ((st = upload_tables(b, ws))) return st;
+        const long long nch = fill_starts(b, ws, chunks_of);
+        if ((st = ensure_parts(b, nch))) return st;
+        if ((st = upload_starts(b, ws.size()))) return st;
+        k_bresidual<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_starts, (int)ws.size(),
+                                                          b->d_parts);
+        b->launches += 1;
+        BCK(cudaGetLastError());
+        if ((st = reduce_windows(b, ws.size()))) return st;
+        if (timed) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, b->e0, b->e1) == cudaSuccess) b->sweep_ms += ms;
+            timed = false;
+        }
+        std::vector<SolveItem *> next;
+        for (size_t i = 0; i < act.size(); ++i) {
+            SolveItem *a = act[i];
+            const double rn = std::sqrt(b->h_out[3 * i]);
+            a->w->last_res_rel = a->bnorm > 0 ? rn / a->bnorm : rn;
+            if (!std::isfinite(rn)) {
+                a->done = true;
+                a->ok = false;
+                a->w->err = "residual is not finite";
+                continue;
+            }
+            if (rn <= tol * a->bnorm) {
+                a->done = true;
+                a->ok = true;
+                a->iters = it;
+                continue;
+            }
+            if (it >= max_iters) {
+                a->done = true;
+                a->ok = false;
+                a->iters = it;
+                a->w->err = "solve reached max_iters";
+                continue;
+            }
+            next.push_back(a);
+        }
+        act.swap(next);
+        if (act.empty()) break;
+        ws.clear();
+        for (auto *a : act) ws.push_back(a->w);
+        if ((st = upload_tables(b, ws))) return st;
+        const long long ntiles = fill_starts(b, ws, [](const Window &w) { return win_tiles(w.L); });
+        if ((st = upload_starts(b, ws.size()))) return st;
+        const int n = std::min(check_every, max_iters - it);
+        BCK(cudaEventRecord(b->e0, b->stream));
+        for (int s = 0; s < n; ++s) {
+            k_bsweep<0><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_starts,
+                                                                 (int)ws.size(), (float)omega);
+            k_bsweep<1><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_starts,
+                                                                 (int)ws.size(), (float)omega);
+        }
+        b->launches += 2LL * n;
+        BCK(cudaGetLastError());
+        BCK(cudaEventRecord(b->e1, b->stream));
+        timed = true;
+        sweeps_total += (long long)n * (long long)act.size();
+        it += n;
+    }
+    return SEG4D_OK;
+}
+
+seg4d_status batch_rescale(seg4d_batch *b, const std::vector<Window *> &ws)
+{
+    std::vector<Window *> with;
+    for (auto *w : ws)
+        if (w->d.nseeds > 0) with.push_back(w);
+    if (with.empty()) return SEG4D_OK;
+    seg4d_status st;
+    if ((st = upload_tables(b, with))) return st;
+    const long long nsd = fill_starts(b, with, [](const Window &w) { return (long long)w.d.nseeds; });
+    if ((st = upload_starts(b, with.size()))) return st;
+    const double r2 = b->p.r_ball * b->p.r_ball;
+    k_bball_minmax<<<(unsigned)nsd, 256, 0, b->stream>>>(b->d_wins, b->d_starts, (int)with.size(), r2);
+    k_brescale_apply<<<(unsigned)nsd, 256, 0, b->stream>>>(b->d_wins, b->d_starts, (int)with.size(),
+                                                           r2);
+    b->launches += 2;
+    BCK(cudaGetLastError());
+    return SEG4D_OK;
+}
+
+seg4d_status upload_seed_table(seg4d_batch *b, Window &w)
+{
+    const int n = (int)w.seeds.size();
+    if (n == 0) return SEG4D_OK;
+    std::vector<SeedDev> sd(n);
+    const double rad = std::max(b->p.r_ball, b->p.R_init) + 1.0;
+    for (int m = 0; m < n; ++m) {
+        const seg4d_seed &s = w.seeds[m];
+        SeedDev &d = sd[m];
+        d.x = s.x;
+        d.y = s.y;
+        d.z = s.z;
+        d.frame = s.frame;
+        auto lo = [&](double c, int nmax) {
+            double v = std::ceil(c - rad);
+            return (int)std::max(0.0, std::min(v, (double)nmax));
+        };
+        auto hi = [&](double c, int nmax) {
+            double v = std::floor(c + rad);
+            return (int)std::min((double)(nmax - 1), std::max(v, -1.0));
+        };
+        d.bx0 = lo(s.x, w.dims.n1);
+        d.bx1 = hi(s.x, w.dims.n1);
+        d.by0 = lo(s.y, w.dims.n2);
+        d.by1 = hi(s.y, w.dims.n2);
+        d.bz0 = lo(s.z, w.dims.n3);
+        d.bz1 = hi(s.z, w.dims.n3);
+    }
+    BCK(cudaMemcpyAsync(w.d.seeds, sd.data(), sizeof(SeedDev) * n, cudaMemcpyHostToDevice,
+                        b->stream));
+    // the host copy `sd` must outlive the copy
+    BCK(cudaStreamSynchronize(b->stream));
+    return SEG4D_OK;
+}
+
+// set-up of the pending windows: owners, thresholding, presmoothing (batched
+// solves), face G, u0 and its rescale.  Image blocks are released at the end.
+seg4d_status batch_setup(seg4d_batch *b, std::vector<Window *> &pend, long long &sweeps)
+{
+    seg4d_status st;
+    const seg4d_params &p = b->p;
+    for (Window *w : pend) {
+        const Layout &L = w->L;
+        const size_t S2 = 2 * (size_t)L.S;
+        if ((st = upload_seed_table(b, *w))) return st;
+        BCK(cudaMemsetAsync(w->d.owner, 0x7F, S2 * sizeof(int), b->stream));
+        if (w->d.nseeds > 0) {
+            // owner distance keys live in the (not yet used) presmoothing arrays
+            unsigned long long *dkey = (unsigned long long *)w->Is0;
+            BCK(cudaMemsetAsync(dkey, 0xFF, S2 * sizeof(unsigned long long), b->stream));
+            launch_owner(L, w->d.seeds, w->d.nseeds, p.r_ball, dkey, w->d.owner, b->stream);
+        }
+        BCK(cudaMemcpyAsync(w->ITH, w->I0, S2 * sizeof(float), cudaMemcpyDeviceToDevice, b->stream));
+        if (w->d.nseeds > 0) {
+            launch_ball_minmax(L, w->d.seeds, w->d.nseeds, p.r_ball, w->I0, w->d.stat, b->stream);
+            launch_threshold_apply(L, w->d.seeds, w->d.nseeds, p.r_ball, p.lambda_th, w->d.stat,
+                                   w->d.owner, w->I0, w->ITH, b->stream);
+            b->launches += 4;
+        }
+        BCK(cudaGetLastError());
+    }
+    // two batched presmoothing solves: I0 -> Is0, ITH -> IsTH
+    const float4 ih2 = make_float4((float)(1.0 / (p.h[0] * p.h[0])), (float)(1.0 / (p.h[1] * p.h[1])),
+                                   (float)(1.0 / (p.h[2] * p.h[2])), (float)(1.0 / (p.h[3] * p.h[3])));
+    for (int img = 0; img < 2; ++img) {
+        std::vector<Window *> ws;
+        for (Window *w : pend) {
+            float *src = img == 0 ? w->I0 : w->ITH;
+            float *dst = img == 0 ? w->Is0 : w->IsTH;
+            BCK(cudaMemcpyAsync(dst, src, 2 * (size_t)w->L.S * sizeof(float),
+                                cudaMemcpyDeviceToDevice, b->stream));
+            w->d.x = dst;
+            ws.push_back(w);
+        }
+        if ((st = upload_tables(b, ws))) return st;
+        const long long nch = fill_starts(b, ws, chunks_of);
+        if ((st = ensure_parts(b, nch))) return st;
+        if ((st = upload_starts(b, ws.size()))) return st;
+        k_bsmooth_coef<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_starts, (int)ws.size(),
+                                                             ih2, (float)p.sigma_t, b->d_parts);
+        b->launches += 1;
+        BCK(cudaGetLastError());
+        if ((st = reduce_windows(b, ws.size()))) return st;
+        std::vector<SolveItem> items;
+        for (size_t i = 0; i < ws.size(); ++i)
+            items.push_back(SolveItem{ws[i], std::sqrt(b->h_out[3 * i]), 0, false, false});
+        if ((st = batch_solve(b, items, p.omega_smooth, p.tol_smooth, p.max_iters, p.check_every,
+                              sweeps)))
+            return st;
+        for (auto &itm : items)
+            if (!itm.ok) itm.w->state = kFailed;
+    }
+    for (Window *w : pend) {
+        w->d.x = w->d.u;
+        if (w->state == kFailed) continue;
+        launch_face_G(w->L, w->Is0, w->IsTH, p.h, p.K, p.delta, p.vartheta, w->d.G, b->stream);
+        BCK(cudaMemsetAsync(w->d.u, 0, 2 * (size_t)w->L.S * sizeof(float), b->stream));
+        launch_init_u(w->L, w->d.seeds, w->d.nseeds, p.R_init, p.v_init, w->d.u, b->stream);
+        b->launches += 2;
+        BCK(cudaGetLastError());
+    }
+    std::vector<Window *> ok;
+    for (Window *w : pend)
+        if (w->state != kFailed) ok.push_back(w);
+    if ((st = batch_rescale(b, ok))) return st;
+    BCK(cudaStreamSynchronize(b->stream));
+    for (Window *w : pend) {
+        if (w->has_img) {
+            b->arena.release(w->off_img, w->bytes_img);
+            w->has_img = false;
+        }
+        if (w->state != kFailed) w->state = kActive;
+    }
+    return SEG4D_OK;
+}
+
+seg4d_status batch_step(seg4d_batch *b, std::vector<Window *> &act, long long &sweeps)
+{
+    const seg4d_params &p = b->p;
+    seg4d_status st;
+    for (Window *w : act) w->d.x = w->d.u;
+    if ((st = upload_tables(b, act))) return st;
+    const long long nch = fill_starts(b, act, chunks_of);
+    if ((st = ensure_parts(b, nch))) return st;
+    if ((st = upload_starts(b, act.size()))) return st;
+    StepConst K;
+    for (int d = 0; d < 4; ++d) {
+        K.inv_h[d] = (float)(1.0 / p.h[d]);
+        K.inv_h2[d] = (float)(1.0 / (p.h[d] * p.h[d]));
+    }
+    K.tau = (float)p.tau;
+    K.eps2 = (float)(p.eps * p.eps);
+    k_bcoef<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_starts, (int)act.size(), K,
+                                                  b->d_parts);
+    b->launches += 1;
+    BCK(cudaGetLastError());
+    if ((st = reduce_windows(b, act.size()))) return st;
+    std::vector<SolveItem> items;
+    for (size_t i = 0; i < act.size(); ++i)
+        items.push_back(SolveItem{act[i], std::sqrt(b->h_out[3 * i]), 0, false, false});
+    if ((st = batch_solve(b, items, p.omega, p.tol, p.max_iters, p.check_every, sweeps))) return st;
+    std::vector<Window *> ok;
+    for (auto &itm : items) {
+        itm.w->last_iters = itm.iters;
+        itm.w->sweeps += itm.iters;
+        if (itm.ok)
+            ok.push_back(itm.w);
+        else
+            itm.w->state = kFailed;
+    }
+    if ((st = batch_rescale(b, ok))) return st;
+    for (Window *w : ok) {
+        w->steps_done += 1;
+        if (w->steps_done >= w->nsteps) w->state = kDone;
+    }
+    return SEG4D_OK;
+}
+
+void batch_free(seg4d_batch *b)
+{
+    cudaFree(b->arena_mem);
+    cudaFree(b->d_wins);
+    cudaFree(b->d_starts);
+    cudaFree(b->d_out);
+    cudaFree(b->d_parts);
+    if (b->h_wins) cudaFreeHost(b->h_wins);
+    if (b->h_starts) cudaFreeHost(b->h_starts);
+    if (b->h_out) cudaFreeHost(b->h_out);
+    if (b->e0) cudaEventDestroy(b->e0);
+    if (b->e1) cudaEventDestroy(b->e1);
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+seg4d_status seg4d_batch_create(size_t arena_bytes, int max_windows, void *cuda_stream,
+                                seg4d_batch **out)
+{
+    handle_free_error().clear();
+    if (!out || max_windows < 1 || arena_bytes < (1u << 20)) {
+        handle_free_error() = "batch_create: out != NULL, max_windows >= 1, arena >= 1 MiB";
+        return SEG4D_ERR_INVALID;
+    }
+    *out = nullptr;
+    seg4d_batch *b = new (std::nothrow) seg4d_batch();
+    if (!b) return SEG4D_ERR_OOM;
+    cudaGetDevice(&b->device);
+    b->stream = (cudaStream_t)cuda_stream;
+    seg4d_default_params(&b->p);
+    b->max_windows = max_windows;
+    const size_t arena = align_up(arena_bytes);
+    bool ok = cudaMalloc(&b->arena_mem, arena) == cudaSuccess &&
+              cudaMalloc(&b->d_wins, sizeof(BWin) * max_windows) == cudaSuccess &&
+              cudaMalloc(&b->d_starts, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaMalloc(&b->d_out, 3 * sizeof(double) * max_windows) == cudaSuccess &&
+              cudaMallocHost(&b->h_wins, sizeof(BWin) * max_windows) == cudaSuccess &&
+              cudaMallocHost(&b->h_starts, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaMallocHost(&b->h_out, 3 * sizeof(double) * max_windows) == cudaSuccess &&
+              cudaEventCreate(&b->e0) == cudaSuccess && cudaEventCreate(&b->e1) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        batch_free(b);
+        delete b;
+        handle_free_error() = "batch_create: device allocation failed";
+        return SEG4D_ERR_OOM;
+    }
+    b->arena.init(b->arena_mem, arena);
+    *out = b;
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_batch_destroy(seg4d_batch *b)
+{
+    if (!b) return SEG4D_OK;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_batch_set_params(seg4d_batch *b, const seg4d_params *p)
+{
+    if (!b || !p) return SEG4D_ERR_INVALID;
+    // the same validation as the single-grid handle
+    if (p->precision != 0 || !(p->omega > 0 && p->omega < 2) ||
+        !(p->omega_smooth > 0 && p->omega_smooth < 2) || !(p->tol > 0) || !(p->tol_smooth > 0) ||
+        p->max_iters < 1 || p->check_every < 1 || !(p->tau > 0) || !(p->eps > 0) ||
+        !(p->sigma_t > 0) || !(p->r_ball > 0) || !(p->R_init > 0) || !(p->v_init > 0))
+        return bfail(b, SEG4D_ERR_INVALID, "batch_set_params: invalid parameters");
+    for (int d = 0; d < 4; ++d)
+        if (!(p->h[d] > 0) || !std::isfinite(p->h[d]))
+            return bfail(b, SEG4D_ERR_INVALID, "batch_set_params: h must be > 0");
+    b->p = *p;
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_batch_add(seg4d_batch *b, const seg4d_dims *dims, const float *image,
+                             int on_device, const seg4d_seed *seeds, int nseeds, int nsteps,
+                             int *id_out)
+{
+    if (!b) return SEG4D_ERR_INVALID;
+    if (!dims || dims->n1 < 1 || dims->n2 < 1 || dims->n3 < 1 || dims->n4 < 1 ||
+        dims->n3 > 65535 || dims->n4 > 65535 || !image || nseeds < 0 || (nseeds && !seeds) ||
+        nsteps < 0 || !id_out)
+        return bfail(b, SEG4D_ERR_INVALID, "batch_add: invalid arguments");
+    if ((int)b->wins.size() >= b->max_windows)
+        return bfail(b, SEG4D_ERR_OOM, "batch_add: window table full");
+    for (int m = 0; m < nseeds; ++m)
+        if (!std::isfinite(seeds[m].x) || !std::isfinite(seeds[m].y) || !std::isfinite(seeds[m].z))
+            return bfail(b, SEG4D_ERR_INVALID, "batch_add: seed coordinates must be finite");
+    Window w;
+    w.id = b->next_id;
+    w.dims = *dims;
+    w.L = layout_of(*dims);
+    w.seeds.assign(seeds, seeds + nseeds);
+    w.nsteps = nsteps;
+    w.bytes_main = main_bytes(w.L, nseeds);
+    w.bytes_img = img_bytes(w.L);
+    if (!b->arena.alloc(w.bytes_main, w.off_main))
+        return bfail(b, SEG4D_ERR_OOM, "batch_add: no room in the arena (admission refused)");
+    if (!b->arena.alloc(w.bytes_img, w.off_img)) {
+        b->arena.release(w.off_main, w.bytes_main);
+        return bfail(b, SEG4D_ERR_OOM, "batch_add: no room in the arena (admission refused)");
+    }
+    w.has_img = true;
+    carve(b, w);
+    // zero the main block (padding slots must read as zero)
+    BCK(cudaMemsetAsync(b->arena.base + w.off_main, 0, w.bytes_main, b->stream));
+    BCK(cudaMemsetAsync(b->arena.base + w.off_img, 0, w.bytes_img, b->stream));
+    const size_t n = (size_t)dims->n1 * dims->n2 * dims->n3 * dims->n4;
+    const float *nat = image;
+    if (!on_device) {
+        // stage the natural-layout image in the (still unused) ITH..IsTH area
+        BCK(cudaMemcpyAsync(w.Is0, image, n * sizeof(float), cudaMemcpyHostToDevice, b->stream));
+        nat = w.Is0;
+    }
+    launch_split_from_natural(w.L, nat, w.I0, b->stream);
+    b->launches += 1;
+    BCK(cudaGetLastError());
+    BCK(cudaStreamSynchronize(b->stream));
+    b->next_id += 1;
+    *id_out = w.id;
+    b->wins[w.id] = w;
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_batch_advance(seg4d_batch *b, seg4d_batch_info *info)
+{
+    if (!b) return SEG4D_ERR_INVALID;
+    if (info) std::memset(info, 0, sizeof(*info));
+    b->launches = 0;
+    b->sweep_ms = 0.0;
+    long long sweeps = 0;
+    seg4d_status st;
+    cudaEvent_t c0, c1;
+    cudaEventCreate(&c0);
+    cudaEventCreate(&c1);
+    cudaEventRecord(c0, b->stream);
+    std::vector<Window *> pend, act;
+    for (auto &kv : b->wins) {
+        if (kv.second.state == kPending) pend.push_back(&kv.second);
+    }
+    if (!pend.empty() && (st = batch_setup(b, pend, sweeps))) goto out;
+    for (auto &kv : b->wins)
+        if (kv.second.state == kActive && kv.second.steps_done < kv.second.nsteps)
+            act.push_back(&kv.second);
+    for (auto &kv : b->wins)
+        if (kv.second.state == kActive && kv.second.steps_done >= kv.second.nsteps)
+            kv.second.state = kDone;
+    if (!act.empty() && (st = batch_step(b, act, sweeps))) goto out;
+    st = SEG4D_OK;
+out:
+    cudaEventRecord(c1, b->stream);
+    float ms = 0.0f;
+    if (cudaEventSynchronize(c1) == cudaSuccess) cudaEventElapsedTime(&ms, c0, c1);
+    cudaEventDestroy(c0);
+    cudaEventDestroy(c1);
+    if (info) {
+        info->setup_windows = (int)pend.size();
+        info->stepped_windows = (int)act.size();
+        info->window_sweeps = sweeps;
+        info->ms = ms;
+        info->sweep_ms = b->sweep_ms;
+        info->launches = b->launches;
+        int a = 0, d = 0, f = 0;
+        for (auto &kv : b->wins) {
+            a += kv.second.state == kActive || kv.second.state == kPending;
+            d += kv.second.state == kDone;
+            f += kv.second.state == kFailed;
+        }
+        info->active_windows = a;
+        info->done_windows = d;
+        info->failed_windows = f;
+        info->arena_used = b->arena.used;
+        info->status = st;
+    }
+    return st;
+}
+
+seg4d_status seg4d_batch_poll(seg4d_batch *b, int id, seg4d_window_info *wi)
+{
+    if (!b || !wi) return SEG4D_ERR_INVALID;
+    auto it = b->wins.find(id);
+    if (it == b->wins.end()) return bfail(b, SEG4D_ERR_INVALID, "batch_poll: unknown window");
+    const Window &w = it->second;
+    std::memset(wi, 0, sizeof(*wi));
+    wi->state = w.state;
+    wi->steps_done = w.steps_done;
+    wi->nsteps = w.nsteps;
+    wi->sweeps = w.sweeps;
+    wi->last_iters = w.last_iters;
+    wi->last_res_rel = w.last_res_rel;
+    wi->device_bytes = (long long)(w.bytes_main + (w.has_img ? w.bytes_img : 0));
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_batch_read_u(seg4d_batch *b, int id, float *dst, size_t n, int on_device)
+{
+    if (!b || !dst) return SEG4D_ERR_INVALID;
+    auto it = b->wins.find(id);
+    if (it == b->wins.end()) return bfail(b, SEG4D_ERR_INVALID, "batch_read_u: unknown window");
+    Window &w = it->second;
+    const size_t nv = (size_t)w.dims.n1 * w.dims.n2 * w.dims.n3 * w.dims.n4;
+    if (n != nv) return bfail(b, SEG4D_ERR_INVALID, "batch_read_u: size mismatch");
+    if (w.state == kPending) return bfail(b, SEG4D_ERR_STATE, "batch_read_u: set-up not run yet");
+    if (on_device) {
+        launch_natural_from_split(w.L, w.d.u, dst, b->stream);
+        BCK(cudaGetLastError());
+        BCK(cudaStreamSynchronize(b->stream));
+        return SEG4D_OK;
+    }
+    // stage through the diag array (free between steps)
+    launch_natural_from_split(w.L, w.d.u, w.d.diag, b->stream);
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(dst, w.d.diag, n * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return SEG4D_OK;
+}
+
+seg4d_status seg4d_batch_remove(seg4d_batch *b, int id)
+{
+    if (!b) return SEG4D_ERR_INVALID;
+    auto it = b->wins.find(id);
+    if (it == b->wins.end()) return bfail(b, SEG4D_ERR_INVALID, "batch_remove: unknown window");
+    BCK(cudaStreamSynchronize(b->stream));
+    Window &w = it->second;
+    b->arena.release(w.off_main, w.bytes_main);
+    if (w.has_img) b->arena.release(w.off_img, w.bytes_img);
+    b->wins.erase(it);
+    return SEG4D_OK;
+}
+
+size_t seg4d_batch_window_bytes(const seg4d_dims *dims, int nseeds)
+{
+    if (!dims || dims->n1 < 1 || dims->n2 < 1 || dims->n3 < 1 || dims->n4 < 1) return 0;
+    const Layout L = layout_of(*dims);
+    return main_bytes(L, nseeds) + img_bytes(L);
+}
+
+const char *seg4d_batch_last_error(const seg4d_batch *b)
+{
+    if (!b) return handle_free_error().c_str();
+    return b->err.c_str();
+}
+
+}  // extern "C"

@@ -147,3 +147,51 @@ def small_nuclei(seed: int, n=(40, 36, 20, 6), count: int = 4, nsteps: int = 3) 
 def random_field(seed: int, n, lo=0.0, hi=1.0) -> np.ndarray:
     n1, n2, n3, n4 = n
     return np.random.default_rng(seed).uniform(lo, hi, size=(n4, n3, n2, n1)).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# per-nucleus windows (batched / served workloads)
+# --------------------------------------------------------------------------
+
+def _cut(volume: Case, a: int, edge, frames: int):
+    """Window of spatial size edge (x, y, z) and `frames` frames around
+    nucleus a of `volume`, starting at frame 0, shifted to lie inside."""
+    n4, n3, n2, n1 = volume.image.shape
+    ex, ey, ez = (min(int(e), m) for e, m in zip(edge, (n1, n2, n3)))
+    fr = min(int(frames), n4)
+    c = volume.meta["paths"][a, 0]
+    x0 = int(np.clip(round(c[0]) - ex // 2, 0, n1 - ex))
+    y0 = int(np.clip(round(c[1]) - ey // 2, 0, n2 - ey))
+    z0 = int(np.clip(round(c[2]) - ez // 2, 0, n3 - ez))
+    img = np.ascontiguousarray(volume.image[:fr, z0:z0 + ez, y0:y0 + ey, x0:x0 + ex])
+    seed = np.array([[np.clip(round(c[0]) - x0, 0, ex - 1), np.clip(round(c[1]) - y0, 0, ey - 1),
+                      np.clip(round(c[2]) - z0, 0, ez - 1), 0]], dtype=np.float64)
+    return img, seed
+
+
+def windows(count: int, seed: int = 4, edge=(24, 64), frames=(8, 16), nsteps: int = 30,
+            volumes: int = 2):
+    """`count` per-nucleus windows cut from `volumes` medium-generator volumes
+    (seeds seed, seed+1, ...): cubic spatial edge uniform in `edge`, frame
+    count uniform in `frames`, one seed at the nucleus centre in frame 0.
+    Returns a list of (image, seeds, nsteps)."""
+    rng = np.random.default_rng(seed)
+    vols = [nuclei(seed + v, (128, 128, 64, 32), count=60, nsteps=nsteps) for v in range(volumes)]
+    out = []
+    for k in range(count):
+        vol = vols[k % volumes]
+        a = (k // volumes) % vol.meta["count"]
+        e = int(rng.integers(edge[0], edge[1] + 1))
+        f = int(rng.integers(frames[0], frames[1] + 1))
+        img, s = _cut(vol, a, (e, e, e), f)
+        out.append((img, s, nsteps))
+    return out
+
+
+def request_sizes(count: int, seed: int = 5, lo: float = 16.0, hi: float = 96.0):
+    """Window edges log-uniform in [lo, hi] with frames = round(edge/4): the
+    sizes of the served requests (16^3 x 4 to 96^3 x 24)."""
+    rng = np.random.default_rng(seed)
+    e = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count))
+    edges = np.rint(e).astype(int)
+    return [(int(s), int(s), int(s), max(1, int(round(s / 4)))) for s in edges]
