@@ -183,6 +183,110 @@ def _config(case):
             "parallelism": "replicas", "l2": "inputs larger than L2 (about 3 GB resident)"}
 
 
+def _plain_window(img_d, seeds, nsteps, params):
+    """The plain per-instance FP32 path: one handle per window."""
+    from paper_2111_11866_gb300 import _lib
+    n4, n3, n2, n1 = img_d.shape
+    import torch
+    out = torch.empty_like(img_d)
+    with _lib.Seg4D((n1, n2, n3, n4), stream=torch.cuda.current_stream(), params=params) as s:
+        s.set_image(img_d)
+        s.set_seeds(seeds)
+        s.step(nsteps)
+        s.read_u(out)
+    return out
+
+
+def run_batched(nwin, nsteps, params, plain_sample=48):
+    """Per-nucleus windows (edge U[24,64], 8-16 frames) advanced by the batch
+    engine with continuous admission under a device budget, against the plain
+    per-window path on a sample of the same windows, at the same tolerance."""
+    import numpy as np
+    import torch
+    from paper_2111_11866_gb300 import _lib, serve, synth
+    ws = synth.windows(nwin, nsteps=nsteps)
+    dev = [torch.from_numpy(w[0]).cuda() for w in ws]
+    need = sum(_lib.Batch.window_bytes((w[0].shape[3], w[0].shape[2], w[0].shape[1],
+                                        w[0].shape[0]), 1) for w in ws)
+    budget = int(min(need * 1.05 + (64 << 20), 200e9))
+    reqs = [serve.Request(k, 0.0, dev[k], ws[k][1], nsteps) for k in range(nwin)]
+    torch.cuda.synchronize()
+    with serve.Server(budget, min(nwin, 8192), params=params) as srv:
+        t0 = time.perf_counter()
+        st = srv.run(reqs, sync=None)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+    nplain = min(plain_sample, nwin)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_out = [_plain_window(dev[k], ws[k][1], nsteps, params) for k in range(nplain)]
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    # accuracy check on a few windows: batched result vs plain result
+    maxdiff = 0.0
+    with _lib.Batch(int(need / nwin * 8 + (64 << 20)), 8, params=params) as b:
+        for k in range(min(4, nplain)):
+            wid = b.add(dev[k], ws[k][1], nsteps)
+            for _ in range(nsteps):
+                b.advance()
+            u = b.read_u(wid)
+            ref = plain_out[k].cpu().numpy()
+            maxdiff = max(maxdiff, float(np.abs(u - ref).max() / max(np.abs(ref).max(), 1e-30)))
+            b.remove(wid)
+    vox = sum(w[0].size for w in ws)
+    return {"workload": f"{nwin} per-nucleus windows, edge U[24,64], 8-16 frames, {nsteps} steps",
+            "voxels": vox, "budget_gb": budget / 1e9, "seconds": tb,
+            "seg_per_s": st.served / tb, "window_sweeps": st.window_sweeps, "launches": st.launches,
+            "max_resident": st.max_resident, "failed": st.failed,
+            "plain": {"windows": nplain, "seconds": tp, "seg_per_s": nplain / tp},
+            "speedup_vs_plain": (st.served / tb) / (nplain / tp),
+            "max_rel_diff_vs_plain": maxdiff, "dtype": "f32"}
+
+
+def run_serving(rate, seconds, budget_gb, params, pool=24, plain_sample=8):
+    """Open-loop Poisson requests (window edge log-uniform 16..96, frames =
+    edge/4), continuous batching under a device budget; p50/p99 latency and
+    seg/s at the offered rate, then at half the measured capacity; sequential
+    plain solves of the same windows as the comparison."""
+    import numpy as np
+    import torch
+    from paper_2111_11866_gb300 import serve, synth
+    sizes = synth.request_sizes(pool)
+    imgs = []
+    for k, (e, _, _, f) in enumerate(sizes):
+        img, seeds, nsteps = synth.request_window(1000 + k, e, f, nsteps=30)
+        imgs.append((torch.from_numpy(img).cuda(), seeds, nsteps))
+
+    def requests(r, horizon, seed):
+        t = serve.poisson_arrivals(r, max(1, int(r * horizon)), seed)
+        return [serve.Request(k, float(t[k]), *imgs[k % pool]) for k in range(len(t))]
+
+    budget = int(budget_gb * 1e9)
+    out = {"workload": f"open-loop Poisson, window edge log-uniform 16..96 (frames edge/4), "
+                       f"30 steps, {budget_gb:g} GB admission budget, pool of {pool} images"}
+    with serve.Server(budget, 8192, params=params) as srv:
+        st = srv.run(requests(rate, seconds, 11), horizon_s=seconds)
+        s = st.summary()
+        s["offered_rate"] = rate
+        s["seg_per_s"] = st.served / seconds
+        out["at_offered_rate"] = s
+        cap = max(st.served / seconds, 1e-3)
+    with serve.Server(budget, 8192, params=params) as srv:
+        st = srv.run(requests(0.5 * cap, seconds, 12), horizon_s=4 * seconds)
+        s = st.summary()
+        s["offered_rate"] = 0.5 * cap
+        out["at_half_capacity"] = s
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(plain_sample):
+        _plain_window(*imgs[k % pool], params)
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    out["sequential_plain"] = {"requests": plain_sample, "seg_per_s": plain_sample / tp,
+                               "mean_ms": 1e3 * tp / plain_sample}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,6 +294,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-windows", type=int, default=128,
+                    help="per-nucleus windows of the batched measurement (0 = skip; 4096 = "
+                         "the full batched workload)")
+    ap.add_argument("--batched-steps", type=int, default=30)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests/s")
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="arrival horizon of the serving measurement (0 = skip)")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--sweep-variant", type=int, default=1, choices=[0, 1],
                     help="0 = fused red-black wavefront sweep, 1 = one launch per colour")
     ap.add_argument("--time-steps", type=int, default=None,
@@ -302,6 +414,15 @@ def main():
         v, desc, _ = oracle_sample(case, params)
         cpu = {"value": v, "unit": "voxel-sweeps/s", "cores": 1, "kind": "oracle", "sample": desc}
 
+    seg.close()
+    del img_d
+    torch.cuda.empty_cache()
+    batched = serving = None
+    if args.batched_windows > 0:
+        batched = run_batched(args.batched_windows, args.batched_steps, params)
+    if args.serve_seconds > 0:
+        serving = run_serving(args.serve_rate, args.serve_seconds, args.serve_budget_gb, params)
+
     if rank == 0:
         line = {
             "metric": "voxel-sweeps/s", "value": value, "unit": "voxel-sweeps/s",
@@ -326,9 +447,10 @@ def main():
                     "h2d_bytes_per_step": img_h.nbytes, "d2h_bytes_per_step": out_h.nbytes},
             "gpu_launches": launches,
             "clocks": clocks,
+            "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    seg.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -188,6 +188,15 @@ def windows(count: int, seed: int = 4, edge=(24, 64), frames=(8, 16), nsteps: in
     return out
 
 
+def request_window(seed: int, edge: int, frames: int, nsteps: int = 30):
+    """One served request: a window of edge^3 voxels x `frames` frames holding
+    one nucleus (semi-axes scaled to the window) and a seed at its centre."""
+    e = int(edge)
+    c = nuclei(seed, (e, e, e, int(frames)), count=1, axes=(min(4.0, e / 6), min(9.0, e / 3)),
+               margin=e / 3, nsteps=nsteps, name=f"request {e}^3x{frames}")
+    return c.image, c.seeds, nsteps
+
+
 def request_sizes(count: int, seed: int = 5, lo: float = 16.0, hi: float = 96.0):
     """Window edges log-uniform in [lo, hi] with frames = round(edge/4): the
     sizes of the served requests (16^3 x 4 to 96^3 x 24)."""
