@@ -263,19 +263,9 @@ def run_serving(rate, seconds, budget_gb, params, pool=24, plain_sample=8):
 
     budget = int(budget_gb * 1e9)
     out = {"workload": f"open-loop Poisson, window edge log-uniform 16..96 (frames edge/4), "
-                       f"30 steps, {budget_gb:g} GB admission budget, pool of {pool} images"}
-    with serve.Server(budget, 8192, params=params) as srv:
-        st = srv.run(requests(rate, seconds, 11), horizon_s=seconds)
-        s = st.summary()
-        s["offered_rate"] = rate
-        s["seg_per_s"] = st.served / seconds
-        out["at_offered_rate"] = s
-        cap = max(st.served / seconds, 1e-3)
-    with serve.Server(budget, 8192, params=params) as srv:
-        st = srv.run(requests(0.5 * cap, seconds, 12), horizon_s=4 * seconds)
-        s = st.summary()
-        s["offered_rate"] = 0.5 * cap
-        out["at_half_capacity"] = s
+                       f"30 steps, {budget_gb:g} GB admission budget, pool of {pool} images; "
+                       f"the offered rate saturates the GPU, so latency there is queueing: "
+                       f"stats cover requests completed within the {seconds:g} s horizon"}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(plain_sample):
@@ -284,6 +274,20 @@ def run_serving(rate, seconds, budget_gb, params, pool=24, plain_sample=8):
     tp = time.perf_counter() - t0
     out["sequential_plain"] = {"requests": plain_sample, "seg_per_s": plain_sample / tp,
                                "mean_ms": 1e3 * tp / plain_sample}
+    with serve.Server(budget, 8192, params=params) as srv:
+        st = srv.run(requests(rate, seconds, 11), horizon_s=seconds)
+        s = st.summary()
+        s["offered_rate"] = rate
+        s["seg_per_s"] = st.served / seconds
+        out["at_offered_rate"] = s
+    # the largest sustainable rate is what the saturated service completes
+    cap = st.served / seconds if st.served > 0 else plain_sample / tp
+    out["sustainable_rate"] = cap
+    with serve.Server(budget, 8192, params=params) as srv:
+        st = srv.run(requests(0.5 * cap, seconds, 12), horizon_s=seconds + 20.0)
+        s = st.summary()
+        s["offered_rate"] = 0.5 * cap
+        out["at_half_capacity"] = s
     return out
 
 

@@ -32,8 +32,29 @@ namespace seg4d_impl {
 
 constexpr int kChunkTiles = 16;   // tiles per block of the reduction kernels
 
+// Division of n < 2^31 by a runtime constant d >= 1 with a multiply-high and a
+// shift (round-up method): s = ceil(log2 d), m = ceil(2^(32+s) / d) - 2^32,
+// then n / d = (umulhi(n, m) + n) >> s; the sum stays below 2^32.
+struct FastDiv {
+    unsigned m, s, d, pad;
+};
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    unsigned s = 0;
+    while ((1ull << s) < d) ++s;
+    const unsigned long long m = ((1ull << (32 + s)) + d - 1) / d - (1ull << 32);
+    return FastDiv{(unsigned)m, s, d, 0};
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f)
+{
+    return (__umulhi(n, f.m) + n) >> f.s;
+}
+
 struct BWin {
     Layout L;
+    FastDiv fP, fn2, fn3;          // division by P, n2, n3
     float *x;                      // array the current solve iterates on
     float *u, *beta, *gamma, *diag, *W, *G;
     int *owner;
@@ -43,10 +64,10 @@ struct BWin {
     int pad;
 };
 
-__host__ __device__ inline long long win_tiles(const Layout &L)
-{
-    return (long long)L.nchunk * L.njb * L.n3 * L.n4;
-}
+// A window's (row, slot) pairs of one colour are enumerated linearly,
+// e = row * P + slot, and cut into tiles of 256 consecutive pairs, one tile
+// per block: no lane idles on short rows (small windows have P = 12..32).
+__host__ __device__ inline long long win_tiles(const Layout &L) { return (L.S + 255) / 256; }
 
 // largest w with starts[w] <= b (starts ascending, starts[0] = 0)
 __device__ inline int find_win(const long long *__restrict__ starts, int n, long long b)
@@ -62,20 +83,21 @@ __device__ inline int find_win(const long long *__restrict__ starts, int n, long
     return lo;
 }
 
-// tile t of a window -> thread's (row position, slot); false if outside
-__device__ inline bool tile_pos(const Layout &L, long long t, RowPos &rp, int &s, int &row)
+// tile t of window wd -> thread's (row position, slot); false past the end
+__device__ inline bool tile_pos(const BWin &wd, long long t, RowPos &rp, int &s, int &row)
 {
-    const int chunk = (int)(t % L.nchunk);
-    long long r = t / L.nchunk;
-    const int jb = (int)(r % L.njb);
-    r /= L.njb;
-    rp.k = (int)(r % L.n3);
-    rp.l = (int)(r / L.n3);
-    rp.j = jb * 8 + (int)(threadIdx.x >> 5);
-    s = chunk * 32 + (int)(threadIdx.x & 31);
-    if (rp.j >= L.n2 || s >= L.P) return false;
+    const long long e = t * 256 + threadIdx.x;
+    if (e >= wd.L.S) return false;
+    const unsigned ue = (unsigned)e;
+    const unsigned r = fdiv(ue, wd.fP);
+    s = (int)(ue - r * (unsigned)wd.L.P);
+    const unsigned a = fdiv(r, wd.fn2);
+    rp.j = (int)(r - a * (unsigned)wd.L.n2);
+    const unsigned c = fdiv(a, wd.fn3);
+    rp.k = (int)(a - c * (unsigned)wd.L.n3);
+    rp.l = (int)c;
     rp.p = (rp.j + rp.k + rp.l) & 1;
-    row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
+    row = (int)r;
     return true;
 }
 
@@ -91,7 +113,7 @@ __global__ void __launch_bounds__(256, 8) k_bsweep(const BWin *__restrict__ wins
     const Layout L = wins[w].L;
     RowPos rp;
     int s, row;
-    if (!tile_pos(L, b - starts[w], rp, s, row)) return;
+    if (!tile_pos(wins[w], b - starts[w], rp, s, row)) return;
     if (2 * s + (C ^ rp.p) >= L.n1) return;
     float *x = wins[w].x;
     const float *beta = wins[w].beta, *gamma = wins[w].gamma, *W = wins[w].W;
@@ -120,7 +142,7 @@ __global__ void __launch_bounds__(256) k_bresidual(const BWin *__restrict__ wins
     for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
         RowPos rp;
         int s, row;
-        if (!tile_pos(L, t, rp, s, row)) continue;
+        if (!tile_pos(wins[w], t, rp, s, row)) continue;
         const long long q = (long long)row * L.P + s;
         for (int C = 0; C < 2; ++C) {
             if (2 * s + (C ^ rp.p) >= L.n1) continue;
@@ -165,7 +187,7 @@ __global__ void __launch_bounds__(256) k_bcoef(const BWin *__restrict__ wins,
     for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
         RowPos rp;
         int s, row;
-        if (!tile_pos(L, t, rp, s, row)) continue;
+        if (!tile_pos(wins[w], t, rp, s, row)) continue;
         const long long q = (long long)row * L.P + s;
         for (int C = 0; C < 2; ++C) {
             const int i = 2 * s + (C ^ rp.p);
@@ -218,7 +240,7 @@ __global__ void __launch_bounds__(256) k_bsmooth_coef(const BWin *__restrict__ w
     for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
         RowPos rp;
         int s, row;
-        if (!tile_pos(L, t, rp, s, row)) continue;
+        if (!tile_pos(wins[w], t, rp, s, row)) continue;
         const long long q = (long long)row * L.P + s;
         for (int C = 0; C < 2; ++C) {
             const int i = 2 * s + (C ^ rp.p);
@@ -433,8 +455,16 @@ struct seg4d_batch {
     std::map<int, Window> wins;
     int next_id = 1;
     // device tables (capacity max_windows) and their pinned host mirrors
+    // window table of the current launch set and its offset arrays; the
+    // pinned host copies are not rewritten before their last upload has run
     BWin *d_wins = nullptr, *h_wins = nullptr;
-    long long *d_starts = nullptr, *h_starts = nullptr;
+    long long *d_chunk = nullptr, *h_chunk = nullptr;   // reduction chunks
+    long long *d_tile = nullptr, *h_tile = nullptr;     // sweep tiles
+    long long *d_seed = nullptr, *h_seed = nullptr;     // seed blocks
+    cudaEvent_t ev_table = nullptr;
+    bool table_pending = false;
+    std::vector<std::pair<int, float *>> table_key;     // (window id, x) uploaded
+    long long n_chunk = 0, n_tile = 0, n_seed = 0;
     double *d_out = nullptr, *h_out = nullptr;
     double *d_parts = nullptr;
     size_t parts_cap = 0;    // chunk records
@@ -492,6 +522,9 @@ void carve(seg4d_batch *b, Window &w)
     char *m = b->arena.base + w.off_main;
     float *f = (float *)m;
     w.d.L = w.L;
+    w.d.fP = make_fastdiv((unsigned)w.L.P);
+    w.d.fn2 = make_fastdiv((unsigned)w.L.n2);
+    w.d.fn3 = make_fastdiv((unsigned)w.L.n3);
     w.d.u = f;
     w.d.beta = f + 2 * S;
     w.d.gamma = f + 4 * S;
@@ -513,31 +546,48 @@ void carve(seg4d_batch *b, Window &w)
     w.IsTH = g + 6 * S;
 }
 
-// chunk / tile / seed offsets of a window list into h_starts, returns total
-template <class F>
-long long fill_starts(seg4d_batch *b, const std::vector<Window *> &ws, F count)
+long long chunks_of(const Window &w);
+
+// Make `ws` (in this order) the window table of the following launches:
+// descriptors plus chunk, tile and seed offsets.  Nothing is copied when the
+// same windows with the same solution arrays are already in place.
+seg4d_status set_table(seg4d_batch *b, const std::vector<Window *> &ws)
 {
-    long long acc = 0;
-    for (size_t i = 0; i < ws.size(); ++i) {
-        b->h_starts[i] = acc;
-        acc += count(*ws[i]);
+    std::vector<std::pair<int, float *>> key;
+    key.reserve(ws.size());
+    for (Window *w : ws) key.emplace_back(w->id, w->d.x);
+    if (key == b->table_key) return SEG4D_OK;
+    if (b->table_pending) {
+        BCK(cudaEventSynchronize(b->ev_table));
+        b->table_pending = false;
     }
-    b->h_starts[ws.size()] = acc;
-    return acc;
-}
-
-seg4d_status upload_tables(seg4d_batch *b, const std::vector<Window *> &ws)
-{
-    for (size_t i = 0; i < ws.size(); ++i) b->h_wins[i] = ws[i]->d;
-    BCK(cudaMemcpyAsync(b->d_wins, b->h_wins, sizeof(BWin) * ws.size(), cudaMemcpyHostToDevice,
+    long long c = 0, t = 0, sd = 0;
+    for (size_t i = 0; i < ws.size(); ++i) {
+        b->h_wins[i] = ws[i]->d;
+        b->h_chunk[i] = c;
+        b->h_tile[i] = t;
+        b->h_seed[i] = sd;
+        c += chunks_of(*ws[i]);
+        t += win_tiles(ws[i]->L);
+        sd += ws[i]->d.nseeds;
+    }
+    const size_t n = ws.size();
+    b->h_chunk[n] = c;
+    b->h_tile[n] = t;
+    b->h_seed[n] = sd;
+    b->n_chunk = c;
+    b->n_tile = t;
+    b->n_seed = sd;
+    BCK(cudaMemcpyAsync(b->d_wins, b->h_wins, sizeof(BWin) * n, cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemcpyAsync(b->d_chunk, b->h_chunk, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
                         b->stream));
-    return SEG4D_OK;
-}
-
-seg4d_status upload_starts(seg4d_batch *b, size_t n)
-{
-    BCK(cudaMemcpyAsync(b->d_starts, b->h_starts, sizeof(long long) * (n + 1),
-                        cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemcpyAsync(b->d_tile, b->h_tile, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaMemcpyAsync(b->d_seed, b->h_seed, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaEventRecord(b->ev_table, b->stream));
+    b->table_pending = true;
+    b->table_key.swap(key);
     return SEG4D_OK;
 }
 
@@ -562,7 +612,7 @@ seg4d_status ensure_parts(seg4d_batch *b, long long nchunks)
 // Records of a chunked kernel -> per-window (sum, min, max) in h_out.
 seg4d_status reduce_windows(seg4d_batch *b, size_t nw)
 {
-    k_breduce<<<(unsigned)nw, 256, 0, b->stream>>>(b->d_starts, b->d_parts, b->d_out);
+    k_breduce<<<(unsigned)nw, 256, 0, b->stream>>>(b->d_chunk, b->d_parts, b->d_out);
     b->launches += 1;
     BCK(cudaGetLastError());
     BCK(cudaMemcpyAsync(b->h_out, b->d_out, 3 * sizeof(double) * nw, cudaMemcpyDeviceToHost,
@@ -593,11 +643,10 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
         std::vector<Window *> ws;
         for (auto *a : act) ws.push_back(a->w);
         seg4d_status st;
-        if ((st = upload_tables(b, ws))) return st;
-        const long long nch = fill_starts(b, ws, chunks_of);
+        if ((st = set_table(b, ws))) return st;
+        const long long nch = b->n_chunk;
         if ((st = ensure_parts(b, nch))) return st;
-        if ((st = upload_starts(b, ws.size()))) return st;
-        k_bresidual<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_starts, (int)ws.size(),
+        k_bresidual<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk, (int)ws.size(),
                                                           b->d_parts);
         b->launches += 1;
         BCK(cudaGetLastError());
@@ -637,15 +686,14 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
         if (act.empty()) break;
         ws.clear();
         for (auto *a : act) ws.push_back(a->w);
-        if ((st = upload_tables(b, ws))) return st;
-        const long long ntiles = fill_starts(b, ws, [](const Window &w) { return win_tiles(w.L); });
-        if ((st = upload_starts(b, ws.size()))) return st;
+        if ((st = set_table(b, ws))) return st;
+        const long long ntiles = b->n_tile;
         const int n = std::min(check_every, max_iters - it);
         BCK(cudaEventRecord(b->e0, b->stream));
         for (int s = 0; s < n; ++s) {
-            k_bsweep<0><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_starts,
+            k_bsweep<0><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
                                                                  (int)ws.size(), (float)omega);
-            k_bsweep<1><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_starts,
+            k_bsweep<1><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
                                                                  (int)ws.size(), (float)omega);
         }
         b->launches += 2LL * n;
@@ -660,17 +708,15 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
 
 seg4d_status batch_rescale(seg4d_batch *b, const std::vector<Window *> &ws)
 {
-    std::vector<Window *> with;
-    for (auto *w : ws)
-        if (w->d.nseeds > 0) with.push_back(w);
-    if (with.empty()) return SEG4D_OK;
+    if (ws.empty()) return SEG4D_OK;
     seg4d_status st;
-    if ((st = upload_tables(b, with))) return st;
-    const long long nsd = fill_starts(b, with, [](const Window &w) { return (long long)w.d.nseeds; });
-    if ((st = upload_starts(b, with.size()))) return st;
+    if ((st = set_table(b, ws))) return st;
+    const long long nsd = b->n_seed;
+    if (nsd == 0) return SEG4D_OK;
     const double r2 = b->p.r_ball * b->p.r_ball;
-    k_bball_minmax<<<(unsigned)nsd, 256, 0, b->stream>>>(b->d_wins, b->d_starts, (int)with.size(), r2);
-    k_brescale_apply<<<(unsigned)nsd, 256, 0, b->stream>>>(b->d_wins, b->d_starts, (int)with.size(),
+    // windows without seeds own no block: find_win takes the last equal offset
+    k_bball_minmax<<<(unsigned)nsd, 256, 0, b->stream>>>(b->d_wins, b->d_seed, (int)ws.size(), r2);
+    k_brescale_apply<<<(unsigned)nsd, 256, 0, b->stream>>>(b->d_wins, b->d_seed, (int)ws.size(),
                                                            r2);
     b->launches += 2;
     BCK(cudaGetLastError());
@@ -751,11 +797,10 @@ seg4d_status batch_setup(seg4d_batch *b, std::vector<Window *> &pend, long long 
             w->d.x = dst;
             ws.push_back(w);
         }
-        if ((st = upload_tables(b, ws))) return st;
-        const long long nch = fill_starts(b, ws, chunks_of);
+        if ((st = set_table(b, ws))) return st;
+        const long long nch = b->n_chunk;
         if ((st = ensure_parts(b, nch))) return st;
-        if ((st = upload_starts(b, ws.size()))) return st;
-        k_bsmooth_coef<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_starts, (int)ws.size(),
+        k_bsmooth_coef<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk, (int)ws.size(),
                                                              ih2, (float)p.sigma_t, b->d_parts);
         b->launches += 1;
         BCK(cudaGetLastError());
@@ -798,10 +843,9 @@ seg4d_status batch_step(seg4d_batch *b, std::vector<Window *> &act, long long &s
     const seg4d_params &p = b->p;
     seg4d_status st;
     for (Window *w : act) w->d.x = w->d.u;
-    if ((st = upload_tables(b, act))) return st;
-    const long long nch = fill_starts(b, act, chunks_of);
+    if ((st = set_table(b, act))) return st;
+    const long long nch = b->n_chunk;
     if ((st = ensure_parts(b, nch))) return st;
-    if ((st = upload_starts(b, act.size()))) return st;
     StepConst K;
     for (int d = 0; d < 4; ++d) {
         K.inv_h[d] = (float)(1.0 / p.h[d]);
@@ -809,7 +853,7 @@ seg4d_status batch_step(seg4d_batch *b, std::vector<Window *> &act, long long &s
     }
     K.tau = (float)p.tau;
     K.eps2 = (float)(p.eps * p.eps);
-    k_bcoef<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_starts, (int)act.size(), K,
+    k_bcoef<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk, (int)act.size(), K,
                                                   b->d_parts);
     b->launches += 1;
     BCK(cudaGetLastError());
@@ -839,11 +883,16 @@ void batch_free(seg4d_batch *b)
 {
     cudaFree(b->arena_mem);
     cudaFree(b->d_wins);
-    cudaFree(b->d_starts);
+    cudaFree(b->d_chunk);
+    cudaFree(b->d_tile);
+    cudaFree(b->d_seed);
     cudaFree(b->d_out);
     cudaFree(b->d_parts);
     if (b->h_wins) cudaFreeHost(b->h_wins);
-    if (b->h_starts) cudaFreeHost(b->h_starts);
+    if (b->h_chunk) cudaFreeHost(b->h_chunk);
+    if (b->h_tile) cudaFreeHost(b->h_tile);
+    if (b->h_seed) cudaFreeHost(b->h_seed);
+    if (b->ev_table) cudaEventDestroy(b->ev_table);
     if (b->h_out) cudaFreeHost(b->h_out);
     if (b->e0) cudaEventDestroy(b->e0);
     if (b->e1) cudaEventDestroy(b->e1);
@@ -873,10 +922,15 @@ seg4d_status seg4d_batch_create(size_t arena_bytes, int max_windows, void *cuda_
     const size_t arena = align_up(arena_bytes);
     bool ok = cudaMalloc(&b->arena_mem, arena) == cudaSuccess &&
               cudaMalloc(&b->d_wins, sizeof(BWin) * max_windows) == cudaSuccess &&
-              cudaMalloc(&b->d_starts, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaMalloc(&b->d_chunk, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaMalloc(&b->d_tile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaMalloc(&b->d_seed, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMalloc(&b->d_out, 3 * sizeof(double) * max_windows) == cudaSuccess &&
               cudaMallocHost(&b->h_wins, sizeof(BWin) * max_windows) == cudaSuccess &&
-              cudaMallocHost(&b->h_starts, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaMallocHost(&b->h_chunk, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaMallocHost(&b->h_tile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaMallocHost(&b->h_seed, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaEventCreate(&b->ev_table) == cudaSuccess &&
               cudaMallocHost(&b->h_out, 3 * sizeof(double) * max_windows) == cudaSuccess &&
               cudaEventCreate(&b->e0) == cudaSuccess && cudaEventCreate(&b->e1) == cudaSuccess;
     if (!ok) {

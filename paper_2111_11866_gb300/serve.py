@@ -74,10 +74,17 @@ def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
 
 
 class Server:
+    """`budget_bytes` is the device-memory admission budget (the batch arena).
+    `max_resident_voxels` also caps the voxels in flight: beyond the point
+    where the batched launches saturate the GPU, more resident windows only
+    lengthen every engine iteration (each request needs one iteration per time
+    step), so latency grows with no gain in throughput."""
+
     def __init__(self, budget_bytes: int, max_windows: int = 4096, params=None, stream=None,
-                 keep_results: bool = False):
+                 keep_results: bool = False, max_resident_voxels: float = 64e6):
         self.batch = _lib.Batch(budget_bytes, max_windows, stream=stream, params=params)
         self.keep_results = keep_results
+        self.max_resident_voxels = max_resident_voxels
 
     def close(self):
         self.batch.close()
@@ -96,6 +103,7 @@ class Server:
         pending = list(requests)
         queue: list[Request] = []
         resident: dict[int, Request] = {}
+        resident_vox = 0
         t0 = clock()
         nxt = 0
         while nxt < len(pending) or queue or resident:
@@ -105,9 +113,12 @@ class Server:
             while nxt < len(pending) and pending[nxt].arrival <= now:
                 queue.append(pending[nxt])
                 nxt += 1
-            # FIFO admission while the arena has room
+            # FIFO admission while the arena has room and the voxel cap allows
             while queue:
                 r = queue[0]
+                nv = int(np.prod(r.image.shape))
+                if resident and resident_vox + nv > self.max_resident_voxels:
+                    break
                 wid = self.batch.add(r.image, r.seeds, r.nsteps)
                 if wid is None:
                     st.refused_admissions += 1
@@ -117,6 +128,7 @@ class Server:
                 r.admitted = clock() - t0
                 r.state = "resident"
                 resident[wid] = r
+                resident_vox += nv
             if not resident:
                 # idle until the next arrival
                 if nxt < len(pending):
@@ -137,6 +149,7 @@ class Server:
                 w = self.batch.poll(wid)
                 if w["state"] in ("done", "failed"):
                     r = resident.pop(wid)
+                    resident_vox -= int(np.prod(r.image.shape))
                     r.done = now
                     r.state = w["state"]
                     if w["state"] == "done":

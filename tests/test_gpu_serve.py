@@ -32,9 +32,9 @@ def _requests(n, rate, seed=7):
 def test_served_results_equal_alone_results():
     p = _lib.Params.defaults()
     p.r_ball = p.R_init = 5.0
-    reqs = _requests(8, rate=400.0)
-    # room for about three resident windows: later requests must queue
-    budget = int(3.2 * _lib.Batch.window_bytes((28, 28, 28, 7), 1))
+    reqs = _requests(8, rate=1e6)            # all present at once
+    # room for about two of the largest windows: later requests must queue
+    budget = int(2.2 * _lib.Batch.window_bytes((28, 28, 28, 7), 1))
     with serve.Server(budget, 16, params=p, keep_results=True) as srv:
         stats = srv.run(reqs)
     s = stats.summary()
