@@ -197,21 +197,30 @@ def _plain_window(img_d, seeds, nsteps, params):
     return out
 
 
+def _mixed(params):
+    import copy
+    pm = copy.copy(params)
+    pm.precision = 1
+    return pm
+
+
 def run_batched(nwin, nsteps, params, plain_sample=48):
     """Per-nucleus windows (edge U[24,64], 8-16 frames) advanced by the batch
-    engine with continuous admission under a device budget, against the plain
-    per-window path on a sample of the same windows, at the same tolerance."""
+    engine in mixed precision (BF16 sweep weights, FP32 defect passes) with
+    continuous admission under a device budget, against the plain per-window
+    FP32 path on a sample of the same windows, at the same tolerance."""
     import numpy as np
     import torch
     from paper_2111_11866_gb300 import _lib, serve, synth
+    pm = _mixed(params)
     ws = synth.windows(nwin, nsteps=nsteps)
     dev = [torch.from_numpy(w[0]).cuda() for w in ws]
     need = sum(_lib.Batch.window_bytes((w[0].shape[3], w[0].shape[2], w[0].shape[1],
-                                        w[0].shape[0]), 1) for w in ws)
+                                        w[0].shape[0]), 1, 1) for w in ws)
     budget = int(min(need * 1.05 + (64 << 20), 200e9))
     reqs = [serve.Request(k, 0.0, dev[k], ws[k][1], nsteps) for k in range(nwin)]
     torch.cuda.synchronize()
-    with serve.Server(budget, min(nwin, 8192), params=params) as srv:
+    with serve.Server(budget, min(nwin, 8192), params=pm) as srv:
         t0 = time.perf_counter()
         st = srv.run(reqs, sync=None)
         torch.cuda.synchronize()
@@ -224,7 +233,7 @@ def run_batched(nwin, nsteps, params, plain_sample=48):
     tp = time.perf_counter() - t0
     # accuracy check on a few windows: batched result vs plain result
     maxdiff = 0.0
-    with _lib.Batch(int(need / nwin * 8 + (64 << 20)), 8, params=params) as b:
+    with _lib.Batch(int(need / nwin * 8 + (64 << 20)), 8, params=pm) as b:
         for k in range(min(4, nplain)):
             wid = b.add(dev[k], ws[k][1], nsteps)
             for _ in range(nsteps):
@@ -240,7 +249,8 @@ def run_batched(nwin, nsteps, params, plain_sample=48):
             "max_resident": st.max_resident, "failed": st.failed,
             "plain": {"windows": nplain, "seconds": tp, "seg_per_s": nplain / tp},
             "speedup_vs_plain": (st.served / tb) / (nplain / tp),
-            "max_rel_diff_vs_plain": maxdiff, "dtype": "f32"}
+            "max_rel_diff_vs_plain": maxdiff,
+            "dtype": "mixed: bf16 sweep weights, f32 sweeps and defect passes, f64 norms"}
 
 
 def run_serving(rate, seconds, budget_gb, params, pool=24, plain_sample=8):
@@ -274,7 +284,8 @@ def run_serving(rate, seconds, budget_gb, params, pool=24, plain_sample=8):
     tp = time.perf_counter() - t0
     out["sequential_plain"] = {"requests": plain_sample, "seg_per_s": plain_sample / tp,
                                "mean_ms": 1e3 * tp / plain_sample}
-    with serve.Server(budget, 8192, params=params) as srv:
+    pm = _mixed(params)
+    with serve.Server(budget, 8192, params=pm) as srv:
         st = srv.run(requests(rate, seconds, 11), horizon_s=seconds)
         s = st.summary()
         s["offered_rate"] = rate
@@ -283,7 +294,7 @@ def run_serving(rate, seconds, budget_gb, params, pool=24, plain_sample=8):
     # the largest sustainable rate is what the saturated service completes
     cap = st.served / seconds if st.served > 0 else plain_sample / tp
     out["sustainable_rate"] = cap
-    with serve.Server(budget, 8192, params=params) as srv:
+    with serve.Server(budget, 8192, params=pm) as srv:
         st = srv.run(requests(0.5 * cap, seconds, 12), horizon_s=seconds + 20.0)
         s = st.summary()
         s["offered_rate"] = 0.5 * cap
@@ -413,6 +424,30 @@ def main():
     achieved = per_launch_bytes / (launch_ms / 1000.0) / 1e9 if launch_ms > 0 else None
     kernel_name = SWEEP_KERNELS[params.sweep_variant]
 
+    # the same workload in mixed precision (same handle, same inputs)
+    u_plain = seg.read_u()
+    seg.set_params(precision=1)
+    one_step()
+    mixed_sweeps = 0
+    mixed_sweep_ms = 0.0
+    e0.record(stream)
+    for _ in range(max(1, min(args.steps, 2))):
+        info = one_step()
+        mixed_sweeps += info["sweeps_total"]
+        mixed_sweep_ms += info["sweep_ms"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mixed_ms = e0.elapsed_time(e1)
+    u_mixed = seg.read_u()
+    seg.set_params(precision=0)
+    nm = max(1, min(args.steps, 2))
+    mixed = {"value": nvox * mixed_sweeps / (mixed_ms / 1000.0), "unit": "voxel-sweeps/s",
+             "ms_per_step": mixed_ms / nm, "sweeps_per_segmentation": mixed_sweeps / nm,
+             "sweep_rate": nvox * mixed_sweeps / (mixed_sweep_ms / 1000.0),
+             "max_rel_diff_vs_f32": float(np.abs(u_mixed - u_plain).max() /
+                                          max(np.abs(u_plain).max(), 1e-30)),
+             "dtype": "bf16 sweep weights, f32 sweeps and defect passes, f64 norms"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, _ = oracle_sample(case, params)
@@ -451,6 +486,7 @@ def main():
                     "h2d_bytes_per_step": img_h.nbytes, "d2h_bytes_per_step": out_h.nbytes},
             "gpu_launches": launches,
             "clocks": clocks,
+            "mixed_precision": mixed,
             "batched": batched,
             "serving": serving,
         }

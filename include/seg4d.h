@@ -80,7 +80,12 @@ typedef struct {
                            test; later gaps are predicted from the observed
                            residual decay, within [max(1, check_every/4),
                            8*check_every]                                           */
-    int precision;      /* 0 = FP32 sweeps and coefficients (the only mode so far)  */
+    int precision;      /* 0: FP32 throughout.  1: mixed -- the sweeps stream BF16
+                           face weights (a BF16 system with its own consistent
+                           diagonal) and every check is an exact FP32 defect
+                           pass r = b - A u; the sweeps solve A_b delta = r and
+                           u += delta, so the fixed point is the FP32 system's.
+                           Presmoothing solves are always FP32.                    */
     int sweep_variant;  /* 0 = fused red-black wavefront (one pass per sweep),
                            1 = one launch per colour (default); both give
                            identical bits                                          */
@@ -303,8 +308,9 @@ seg4d_status seg4d_batch_read_u(seg4d_batch *b, int id, float *dst, size_t n, in
 /* Retire window `id` and return its arena space.  Errors: INVALID. */
 seg4d_status seg4d_batch_remove(seg4d_batch *b, int id);
 
-/* Arena bytes a window of these sizes needs at admission. */
-size_t seg4d_batch_window_bytes(const seg4d_dims *dims, int nseeds);
+/* Arena bytes a window of these sizes needs at admission in a batch of the
+ * given precision (seg4d_params.precision). */
+size_t seg4d_batch_window_bytes(const seg4d_dims *dims, int nseeds, int precision);
 
 /* Message of the last error of the batch (NULL: of the last failed create). */
 const char *seg4d_batch_last_error(const seg4d_batch *b);

@@ -325,7 +325,7 @@ SIGNATURES.update({
     "seg4d_batch_poll": (C.c_int, [_P, C.c_int, C.POINTER(CWindowInfo)]),
     "seg4d_batch_read_u": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.c_int]),
     "seg4d_batch_remove": (C.c_int, [_P, C.c_int]),
-    "seg4d_batch_window_bytes": (C.c_size_t, [C.POINTER(CDims), C.c_int]),
+    "seg4d_batch_window_bytes": (C.c_size_t, [C.POINTER(CDims), C.c_int, C.c_int]),
     "seg4d_batch_last_error": (C.c_char_p, [_P]),
 })
 
@@ -431,6 +431,7 @@ class Batch:
         self.shapes.pop(wid, None)
 
     @staticmethod
-    def window_bytes(dims, nseeds=1) -> int:
+    def window_bytes(dims, nseeds=1, precision=0) -> int:
         n1, n2, n3, n4 = dims
-        return int(load().seg4d_batch_window_bytes(C.byref(CDims(n1, n2, n3, n4)), int(nseeds)))
+        return int(load().seg4d_batch_window_bytes(C.byref(CDims(n1, n2, n3, n4)), int(nseeds),
+                                                   int(precision)))

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libseg4d.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "solve_kernels.cu", "setup_kernels.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "solve_kernels.cu", "setup_kernels.cu", "noalloc.cu", "batch.cu",
+           "mixed_kernels.cu"]
 HEADERS = ["seg4d_internal.cuh", "stencil.cuh"]
 
 

@@ -46,6 +46,10 @@ struct seg4d {
     double *host_scal = nullptr;   // pinned mirror of scal
     unsigned *wave_ctrl = nullptr; // fused-sweep control block: 4 + tiles u32
     unsigned *host_wave = nullptr; // pinned: error flag of the last fused sweep
+    // mixed precision (allocated at the first solve with precision 1)
+    void *Wb = nullptr;            // bf16 [8][S] face weights by red end
+    float *gb = nullptr, *ib = nullptr;   // c / D_b and 1 / D_b, [2][S]
+    float *rho = nullptr, *dlt = nullptr; // r / D_b and the correction, [2][S]
     int wave_T = 0;                // tiles per frame of the fused sweep
     int num_sms = 0;
     int wave_occ = 1;              // occupancy limit of the fused sweep (CTAs per SM)
@@ -157,6 +161,11 @@ void free_all(seg4d *h)
     cudaFree(h->scal);
     cudaFree(h->wave_ctrl);
     if (h->host_wave) cudaFreeHost(h->host_wave);
+    cudaFree(h->Wb);
+    cudaFree(h->gb);
+    cudaFree(h->ib);
+    cudaFree(h->rho);
+    cudaFree(h->dlt);
     cudaFree(h->seeds_d);
     cudaFree(h->stat_d);
     if (h->host_scal) cudaFreeHost(h->host_scal);
@@ -201,8 +210,11 @@ struct SolveOut {
 // the per-block records of ||b||^2 must be in `partials` (written by the
 // coefficient kernel).  Stopping rule: ||b - A x||_2 <= tol ||b||_2, tested
 // before the first sweep and after every check_every sweeps.
+// With `mixed` (precision 1) every check is a defect pass (exact residual,
+// right-hand side of the BF16 correction system, delta = 0), the sweeps run
+// on A_b delta = r with BF16 weights and u += delta follows each batch.
 seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_iters,
-                          int check_every, SolveOut &out)
+                          int check_every, SolveOut &out, bool mixed = false)
 {
     const Layout &L = h->L;
     seg4d_status st = reduce_into(h, 0);   // scal[0..2] = sum b^2, min b, max b
@@ -218,8 +230,12 @@ seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_
     int prev_it = 0;
     bool wave_pending = false;
     for (;;) {
-        launch_residual(L, x, h->beta, h->gamma, h->diag, h->W, h->partials, kPartBlocks,
-                        h->stream);
+        if (mixed)
+            launch_defect(L, x, h->beta, h->gamma, h->diag, h->W, h->ib, h->rho, h->dlt,
+                          h->partials, kPartBlocks, h->stream);
+        else
+            launch_residual(L, x, h->beta, h->gamma, h->diag, h->W, h->partials, kPartBlocks,
+                            h->stream);
         h->launches += 1;
         CK_LAUNCH("residual");
         if ((st = reduce_into(h, 3))) return st;   // scal[3..5] = sum r^2, min u, max u
@@ -262,7 +278,16 @@ seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_
         prev_it = it;
         const int n = std::min(batch, max_iters - it);
         CK(cudaEventRecord(h->evs0, h->stream));
-        if (h->p.sweep_variant == 0) {
+        if (mixed) {
+            for (int s = 0; s < n; ++s) {
+                launch_sweep_mixed(L, 0, h->dlt, h->rho, h->gb, h->Wb, (float)omega, h->stream);
+                launch_sweep_mixed(L, 1, h->dlt, h->rho, h->gb, h->Wb, (float)omega, h->stream);
+            }
+            launch_apply(L, x, h->dlt, h->stream);
+            h->launches += 2LL * n + 1;
+            h->sweep_launches += 2LL * n;
+            CK_LAUNCH("sweep_mixed");
+        } else if (h->p.sweep_variant == 0) {
             CK(cudaMemsetAsync(h->wave_ctrl, 0, (4 + h->wave_T) * sizeof(unsigned), h->stream));
             const int per_sm = std::min(h->p.ctas_per_sm > 0 ? h->p.ctas_per_sm : 4, h->wave_occ);
             launch_sweep_wave(L, n, x, h->beta, h->gamma, h->W, (float)omega, h->wave_ctrl,
@@ -282,7 +307,7 @@ seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_
         CK(cudaEventRecord(h->evs1, h->stream));
         timed_batch = true;
         it += n;
-        if (h->p.sweep_variant == 0) {
+        if (!mixed && h->p.sweep_variant == 0) {
             // the flag is read after the next check's synchronisation
             CK(cudaMemcpyAsync(h->host_wave, h->wave_ctrl + 2, sizeof(unsigned),
                                cudaMemcpyDeviceToHost, h->stream));
@@ -433,9 +458,29 @@ seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
     h->launches += 1;
     CK_LAUNCH("step_coef");
     h->has_coef = true;
+    const bool mixed = h->p.precision == 1;
+    if (mixed) {
+        if (!h->Wb) {
+            const size_t S2 = 2 * (size_t)h->L.S;
+            if (cudaMalloc(&h->Wb, 4 * S2 * sizeof(unsigned short)) != cudaSuccess ||
+                cudaMalloc(&h->gb, S2 * sizeof(float)) != cudaSuccess ||
+                cudaMalloc(&h->ib, S2 * sizeof(float)) != cudaSuccess ||
+                cudaMalloc(&h->rho, S2 * sizeof(float)) != cudaSuccess ||
+                cudaMalloc(&h->dlt, S2 * sizeof(float)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, SEG4D_ERR_OOM, "mixed precision arrays: allocation failed");
+            }
+            // padding slots of the correction must read as zero
+            CK(cudaMemsetAsync(h->dlt, 0, S2 * sizeof(float), h->stream));
+            CK(cudaMemsetAsync(h->Wb, 0, 4 * S2 * sizeof(unsigned short), h->stream));
+        }
+        launch_mixed_prepare(h->L, h->W, h->gamma, h->diag, h->Wb, h->gb, h->ib, h->stream);
+        h->launches += 1;
+        CK_LAUNCH("mixed_prepare");
+    }
     SolveOut so;
     seg4d_status st = solve_system(h, h->u, h->p.omega, h->p.tol, h->p.max_iters,
-                                   h->p.check_every, so);
+                                   h->p.check_every, so, mixed);
     if (st) return st;
     sweeps += so.iters;
     if (info) {
@@ -639,7 +684,8 @@ seg4d_status seg4d_set_params(seg4d *h, const seg4d_params *p)
         return fail(h, SEG4D_ERR_INVALID, "tol and tol_smooth must be finite and > 0");
     if (p->max_iters < 1 || p->check_every < 1)
         return fail(h, SEG4D_ERR_INVALID, "max_iters and check_every must be >= 1");
-    if (p->precision != 0) return fail(h, SEG4D_ERR_INVALID, "precision must be 0");
+    if (p->precision != 0 && p->precision != 1)
+        return fail(h, SEG4D_ERR_INVALID, "precision must be 0 or 1");
     if (p->sweep_variant != 0 && p->sweep_variant != 1)
         return fail(h, SEG4D_ERR_INVALID, "sweep_variant must be 0 or 1");
     if (p->ctas_per_sm < 0 || p->ctas_per_sm > 64)

@@ -61,7 +61,9 @@ struct BWin {
     SeedDev *seeds;
     SeedStat *stat;
     int nseeds;
-    int pad;
+    int mixed;                     // precision 1: the arrays below exist
+    __nv_bfloat16 *Wb;             // bf16 [8][S] face weights by red end
+    float *gb, *ib, *rho, *dlt;    // c/D_b, 1/D_b, r/D_b, correction: [2][S]
 };
 
 // A window's (row, slot) pairs of one colour are enumerated linearly,
@@ -265,6 +267,118 @@ __global__ void __launch_bounds__(256) k_bsmooth_coef(const BWin *__restrict__ w
         }
     }
     block_write3(a, parts + 3 * b);
+}
+
+// ---- mixed precision (see mixed_kernels.cu for the scheme)
+
+__global__ void __launch_bounds__(256) k_bmixed_prepare(const BWin *__restrict__ wins,
+                                                        const long long *__restrict__ cstarts,
+                                                        int nwin)
+{
+    const long long b = blockIdx.x;
+    const int w = find_win(cstarts, nwin, b);
+    if (!wins[w].mixed) return;
+    const Layout L = wins[w].L;
+    const float *W = wins[w].W, *gamma = wins[w].gamma, *diag = wins[w].diag;
+    __nv_bfloat16 *Wb = wins[w].Wb;
+    float *gb = wins[w].gb, *ib = wins[w].ib;
+    const long long nt = win_tiles(L);
+    const long long t0 = (b - cstarts[w]) * kChunkTiles;
+    for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
+        RowPos rp;
+        int s, row;
+        if (!tile_pos(wins[w], t, rp, s, row)) continue;
+        const long long q = (long long)row * L.P + s;
+        for (int C = 0; C < 2; ++C) {
+            if (2 * s + (C ^ rp.p) >= L.n1) continue;
+            const float D = diag[C * L.S + q];
+            const float c = gamma[C * L.S + q] * D;
+            const float ex = C ? rounding_excess<1>(L, W, row, s, rp)
+                               : rounding_excess<0>(L, W, row, s, rp);
+            const float Db = D - c * ex;
+            gb[C * L.S + q] = c / Db;
+            ib[C * L.S + q] = 1.0f / Db;
+            if (C == 0)
+                for (int f = 0; f < 8; ++f)
+                    Wb[(long long)f * L.S + q] = __float2bfloat16_rn(W[(long long)f * L.S + q]);
+        }
+    }
+}
+
+// exact residual (records) + rho = r / D_b, delta = 0
+__global__ void __launch_bounds__(256) k_bdefect(const BWin *__restrict__ wins,
+                                                 const long long *__restrict__ cstarts, int nwin,
+                                                 double *__restrict__ parts)
+{
+    const long long b = blockIdx.x;
+    const int w = find_win(cstarts, nwin, b);
+    const Layout L = wins[w].L;
+    const float *x = wins[w].x, *beta = wins[w].beta, *gamma = wins[w].gamma;
+    const float *diag = wins[w].diag, *W = wins[w].W, *ib = wins[w].ib;
+    float *rho = wins[w].rho, *dlt = wins[w].dlt;
+    const long long nt = win_tiles(L);
+    const long long t0 = (b - cstarts[w]) * kChunkTiles;
+    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
+        RowPos rp;
+        int s, row;
+        if (!tile_pos(wins[w], t, rp, s, row)) continue;
+        const long long q = (long long)row * L.P + s;
+        for (int C = 0; C < 2; ++C) {
+            if (2 * s + (C ^ rp.p) >= L.n1) continue;
+            const float acc = C ? neighbour_sum<1>(L, x, W, row, s, rp)
+                                : neighbour_sum<0>(L, x + L.S, W, row, s, rp);
+            const float u = x[C * L.S + q];
+            const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
+            const float r = diag[C * L.S + q] * (ubar - u);
+            rho[C * L.S + q] = r * ib[C * L.S + q];
+            dlt[C * L.S + q] = 0.0f;
+            const double rd = (double)diag[C * L.S + q] * ((double)ubar - (double)u);
+            a.sum += rd * rd;
+            a.mn = fmin(a.mn, (double)u);
+            a.mx = fmax(a.mx, (double)u);
+        }
+    }
+    block_write3(a, parts + 3 * b);
+}
+
+template <int C>
+__global__ void __launch_bounds__(256, 8) k_bsweep_mixed(const BWin *__restrict__ wins,
+                                                         const long long *__restrict__ starts,
+                                                         int nwin, float omega)
+{
+    const long long b = blockIdx.x;
+    const int w = find_win(starts, nwin, b);
+    const Layout L = wins[w].L;
+    RowPos rp;
+    int s, row;
+    if (!tile_pos(wins[w], b - starts[w], rp, s, row)) return;
+    if (2 * s + (C ^ rp.p) >= L.n1) return;
+    float *d = wins[w].dlt;
+    const float *rho = wins[w].rho, *gb = wins[w].gb;
+    const __nv_bfloat16 *Wb = wins[w].Wb;
+    const long long q = (long long)row * L.P + s;
+    const float *dother = d + (C ? 0 : L.S);
+    float *dself = d + (C ? L.S : 0);
+    const float acc = neighbour_sum<C, false, __nv_bfloat16>(L, dother, Wb, row, s, rp);
+    const float dbar = rho[C * L.S + q] + gb[C * L.S + q] * acc;
+    const float d0 = dself[q];
+    dself[q] = d0 + omega * (dbar - d0);
+}
+
+// x <- x + delta on every slot of the tile (padding holds 0 in both)
+__global__ void __launch_bounds__(256) k_bapply(const BWin *__restrict__ wins,
+                                                const long long *__restrict__ starts, int nwin)
+{
+    const long long b = blockIdx.x;
+    const int w = find_win(starts, nwin, b);
+    const long long e = (b - starts[w]) * 256 + threadIdx.x;
+    const long long S = wins[w].L.S;
+    if (e >= S) return;
+    float *x = wins[w].x;
+    const float *d = wins[w].dlt;
+    x[e] += d[e];
+    x[S + e] += d[S + e];
 }
 
 __device__ inline double bseed_d2(const SeedDev &sd, int i, int j, int k)
@@ -506,12 +620,13 @@ Layout layout_of(const seg4d_dims &d)
 
 // main block: u, beta, gamma, diag (2S each), W (8S), G (16S) floats, owner
 // (2S ints), seeds, seed stats; image block: I0, ITH, Is0, IsTH (2S each)
-size_t main_bytes(const Layout &L, int nseeds)
+size_t main_bytes(const Layout &L, int nseeds, bool mixed)
 {
     const size_t S = (size_t)L.S;
     return align_up(32 * S * 4) + align_up(2 * S * 4) +
            align_up(sizeof(SeedDev) * std::max(nseeds, 1)) +
-           align_up(sizeof(SeedStat) * std::max(nseeds, 1));
+           align_up(sizeof(SeedStat) * std::max(nseeds, 1)) +
+           (mixed ? align_up(8 * S * 2) + 4 * align_up(2 * S * 4) : 0);
 }
 
 size_t img_bytes(const Layout &L) { return align_up(8 * (size_t)L.S * 4); }
@@ -537,7 +652,20 @@ void carve(seg4d_batch *b, Window &w)
     w.d.seeds = (SeedDev *)p;
     p += align_up(sizeof(SeedDev) * std::max((int)w.seeds.size(), 1));
     w.d.stat = (SeedStat *)p;
+    p += align_up(sizeof(SeedStat) * std::max((int)w.seeds.size(), 1));
     w.d.nseeds = (int)w.seeds.size();
+    w.d.mixed = b->p.precision == 1;
+    if (w.d.mixed) {
+        w.d.Wb = (__nv_bfloat16 *)p;
+        p += align_up(8 * S * 2);
+        w.d.gb = (float *)p;
+        p += align_up(2 * S * 4);
+        w.d.ib = (float *)p;
+        p += align_up(2 * S * 4);
+        w.d.rho = (float *)p;
+        p += align_up(2 * S * 4);
+        w.d.dlt = (float *)p;
+    }
     w.d.x = w.d.u;
     float *g = (float *)(b->arena.base + w.off_img);
     w.I0 = g;
@@ -633,7 +761,8 @@ struct SolveItem {
 // beta, gamma, diag, W already set up).  Per window: stop when
 // ||b - A x|| <= tol ||b||, tested every check_every sweeps.
 seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double omega, double tol,
-                         int max_iters, int check_every, long long &sweeps_total)
+                         int max_iters, int check_every, long long &sweeps_total,
+                         bool mixed = false)
 {
     std::vector<SolveItem *> act;
     for (auto &it : items) act.push_back(&it);
@@ -646,8 +775,12 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
         if ((st = set_table(b, ws))) return st;
         const long long nch = b->n_chunk;
         if ((st = ensure_parts(b, nch))) return st;
-        k_bresidual<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk, (int)ws.size(),
-                                                          b->d_parts);
+        if (mixed)
+            k_bdefect<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk, (int)ws.size(),
+                                                            b->d_parts);
+        else
+            k_bresidual<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk,
+                                                              (int)ws.size(), b->d_parts);
         b->launches += 1;
         BCK(cudaGetLastError());
         if ((st = reduce_windows(b, ws.size()))) return st;
@@ -691,10 +824,22 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
         const int n = std::min(check_every, max_iters - it);
         BCK(cudaEventRecord(b->e0, b->stream));
         for (int s = 0; s < n; ++s) {
-            k_bsweep<0><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
-                                                                 (int)ws.size(), (float)omega);
-            k_bsweep<1><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
-                                                                 (int)ws.size(), (float)omega);
+            if (mixed) {
+                k_bsweep_mixed<0><<<(unsigned)ntiles, 256, 0, b->stream>>>(
+                    b->d_wins, b->d_tile, (int)ws.size(), (float)omega);
+                k_bsweep_mixed<1><<<(unsigned)ntiles, 256, 0, b->stream>>>(
+                    b->d_wins, b->d_tile, (int)ws.size(), (float)omega);
+            } else {
+                k_bsweep<0><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
+                                                                     (int)ws.size(), (float)omega);
+                k_bsweep<1><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
+                                                                     (int)ws.size(), (float)omega);
+            }
+        }
+        if (mixed) {
+            k_bapply<<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
+                                                              (int)ws.size());
+            b->launches += 1;
         }
         b->launches += 2LL * n;
         BCK(cudaGetLastError());
@@ -857,11 +1002,19 @@ seg4d_status batch_step(seg4d_batch *b, std::vector<Window *> &act, long long &s
                                                   b->d_parts);
     b->launches += 1;
     BCK(cudaGetLastError());
+    const bool mixed = p.precision == 1;
+    if (mixed) {
+        k_bmixed_prepare<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk,
+                                                               (int)act.size());
+        b->launches += 1;
+        BCK(cudaGetLastError());
+    }
     if ((st = reduce_windows(b, act.size()))) return st;
     std::vector<SolveItem> items;
     for (size_t i = 0; i < act.size(); ++i)
         items.push_back(SolveItem{act[i], std::sqrt(b->h_out[3 * i]), 0, false, false});
-    if ((st = batch_solve(b, items, p.omega, p.tol, p.max_iters, p.check_every, sweeps))) return st;
+    if ((st = batch_solve(b, items, p.omega, p.tol, p.max_iters, p.check_every, sweeps, mixed)))
+        return st;
     std::vector<Window *> ok;
     for (auto &itm : items) {
         itm.w->last_iters = itm.iters;
@@ -958,7 +1111,7 @@ seg4d_status seg4d_batch_set_params(seg4d_batch *b, const seg4d_params *p)
 {
     if (!b || !p) return SEG4D_ERR_INVALID;
     // the same validation as the single-grid handle
-    if (p->precision != 0 || !(p->omega > 0 && p->omega < 2) ||
+    if ((p->precision != 0 && p->precision != 1) || !(p->omega > 0 && p->omega < 2) ||
         !(p->omega_smooth > 0 && p->omega_smooth < 2) || !(p->tol > 0) || !(p->tol_smooth > 0) ||
         p->max_iters < 1 || p->check_every < 1 || !(p->tau > 0) || !(p->eps > 0) ||
         !(p->sigma_t > 0) || !(p->r_ball > 0) || !(p->R_init > 0) || !(p->v_init > 0))
@@ -966,6 +1119,9 @@ seg4d_status seg4d_batch_set_params(seg4d_batch *b, const seg4d_params *p)
     for (int d = 0; d < 4; ++d)
         if (!(p->h[d] > 0) || !std::isfinite(p->h[d]))
             return bfail(b, SEG4D_ERR_INVALID, "batch_set_params: h must be > 0");
+    if (!b->wins.empty() && p->precision != b->p.precision)
+        return bfail(b, SEG4D_ERR_INVALID,
+                     "batch_set_params: precision cannot change while windows are resident");
     b->p = *p;
     return SEG4D_OK;
 }
@@ -990,7 +1146,7 @@ seg4d_status seg4d_batch_add(seg4d_batch *b, const seg4d_dims *dims, const float
     w.L = layout_of(*dims);
     w.seeds.assign(seeds, seeds + nseeds);
     w.nsteps = nsteps;
-    w.bytes_main = main_bytes(w.L, nseeds);
+    w.bytes_main = main_bytes(w.L, nseeds, b->p.precision == 1);
     w.bytes_img = img_bytes(w.L);
     if (!b->arena.alloc(w.bytes_main, w.off_main))
         return bfail(b, SEG4D_ERR_OOM, "batch_add: no room in the arena (admission refused)");
@@ -1126,11 +1282,11 @@ seg4d_status seg4d_batch_remove(seg4d_batch *b, int id)
     return SEG4D_OK;
 }
 
-size_t seg4d_batch_window_bytes(const seg4d_dims *dims, int nseeds)
+size_t seg4d_batch_window_bytes(const seg4d_dims *dims, int nseeds, int precision)
 {
     if (!dims || dims->n1 < 1 || dims->n2 < 1 || dims->n3 < 1 || dims->n4 < 1) return 0;
     const Layout L = layout_of(*dims);
-    return main_bytes(L, nseeds) + img_bytes(L);
+    return main_bytes(L, nseeds, precision == 1) + img_bytes(L);
 }
 
 const char *seg4d_batch_last_error(const seg4d_batch *b)

@@ -1,0 +1,182 @@
+// mixed_kernels.cu -- the mixed-precision solve (params.precision = 1).
+//
+// The sweeps stream BF16 face weights wb_f = bf16(w_f) instead of FP32 ones
+// (8 instead of 16 bytes per voxel per colour pass).  The BF16 system A_b
+// keeps the structure of Eq. new1: its diagonal D_b = 1 + c (sum over interior
+// faces of wb_f + sum over boundary faces of w_f) is built from the same
+// rounded weights, so A_b is again a strictly diagonally dominant M-matrix.
+// Accuracy is won back by defect correction against the exact FP32 system A:
+//   r = b - A u             (exact FP32 weights, FP64 norms: the stopping test)
+//   solve A_b delta = r     (red-black SOR on delta from 0, BF16 weights)
+//   u <- u + delta
+// The fixed point is A u = b, the same as the plain FP32 path's.
+#include <cuda_bf16.h>
+
+#include "stencil.cuh"
+
+namespace seg4d_impl {
+
+// Grid-stride over the sweep's 32 x 8 tiles (as in solve_kernels.cu).
+#define MX_FOR_TILES(L, s, rp, row, BODY)                                                  \
+    {                                                                                      \
+        const long long ntile_ = (long long)(L).nchunk * (L).njb * (L).n3 * (L).n4;       \
+        for (long long t_ = blockIdx.x; t_ < ntile_; t_ += gridDim.x) {                    \
+            const int chunk_ = (int)(t_ % (L).nchunk);                                     \
+            long long r_ = t_ / (L).nchunk;                                                \
+            const int jb_ = (int)(r_ % (L).njb);                                           \
+            r_ /= (L).njb;                                                                 \
+            RowPos rp;                                                                     \
+            rp.k = (int)(r_ % (L).n3);                                                     \
+            rp.l = (int)(r_ / (L).n3);                                                     \
+            rp.j = jb_ * 8 + (int)(threadIdx.x >> 5);                                      \
+            const int s = chunk_ * 32 + (int)(threadIdx.x & 31);                           \
+            if (rp.j < (L).n2 && s < (L).P) {                                              \
+                rp.p = (rp.j + rp.k + rp.l) & 1;                                           \
+                const int row = rp.j + (L).n2 * (rp.k + (L).n3 * rp.l);                   \
+                BODY                                                                       \
+            }                                                                              \
+        }                                                                                  \
+    }
+
+// After the FP32 coefficients: Wb = bf16(W) (red ends), and per voxel
+// gamma_b = c / D_b, invD_b = 1 / D_b with D_b = D - c * excess, c = gamma*D.
+__global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__restrict__ W,
+                                                       const float *__restrict__ gamma,
+                                                       const float *__restrict__ diag,
+                                                       __nv_bfloat16 *__restrict__ Wb,
+                                                       float *__restrict__ gb,
+                                                       float *__restrict__ ib)
+{
+    MX_FOR_TILES(L, s, rp, row, {
+        const long long q = (long long)row * L.P + s;
+        for (int C = 0; C < 2; ++C) {
+            if (2 * s + (C ^ rp.p) >= L.n1) continue;
+            const float D = diag[C * L.S + q];
+            const float c = gamma[C * L.S + q] * D;
+            const float ex = C ? rounding_excess<1>(L, W, row, s, rp)
+                               : rounding_excess<0>(L, W, row, s, rp);
+            const float Db = D - c * ex;
+            gb[C * L.S + q] = c / Db;
+            ib[C * L.S + q] = 1.0f / Db;
+            if (C == 0)
+                for (int f = 0; f < 8; ++f)
+                    Wb[(long long)f * L.S + q] = __float2bfloat16_rn(W[(long long)f * L.S + q]);
+        }
+    })
+}
+
+// Exact residual r = D (beta + gamma sum_f W_f u_nb - u) for every voxel;
+// rho = r / D_b, delta = 0; records (sum r^2, min u, max u) in FP64.
+__global__ void __launch_bounds__(kPartThreads) k_defect(Layout L, const float *__restrict__ u,
+                                                         const float *__restrict__ beta,
+                                                         const float *__restrict__ gamma,
+                                                         const float *__restrict__ diag,
+                                                         const float *__restrict__ W,
+                                                         const float *__restrict__ ib,
+                                                         float *__restrict__ rho,
+                                                         float *__restrict__ delta,
+                                                         double *__restrict__ partials)
+{
+    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    MX_FOR_TILES(L, s, rp, row, {
+        const long long q = (long long)row * L.P + s;
+        for (int C = 0; C < 2; ++C) {
+            if (2 * s + (C ^ rp.p) >= L.n1) continue;
+            const float acc = C ? neighbour_sum<1>(L, u, W, row, s, rp)
+                                : neighbour_sum<0>(L, u + L.S, W, row, s, rp);
+            const float uv = u[C * L.S + q];
+            const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
+            const float r = diag[C * L.S + q] * (ubar - uv);
+            rho[C * L.S + q] = r * ib[C * L.S + q];
+            delta[C * L.S + q] = 0.0f;
+            const double rd = (double)diag[C * L.S + q] * ((double)ubar - (double)uv);
+            a.sum += rd * rd;
+            a.mn = fmin(a.mn, (double)uv);
+            a.mx = fmax(a.mx, (double)uv);
+        }
+    })
+    block_write3(a, partials + 3 * blockIdx.x);
+}
+
+// Red-black SOR half sweep on A_b delta = r:
+//   dbar = rho + gamma_b sum_f wb_f delta_nb,  delta <- delta + omega (dbar - delta)
+template <int C>
+__global__ void __launch_bounds__(256, 8) k_sweep_mixed(Layout L, float *__restrict__ d,
+                                                        const float *__restrict__ rho,
+                                                        const float *__restrict__ gb,
+                                                        const __nv_bfloat16 *__restrict__ Wb,
+                                                        float omega)
+{
+    const int chunk = blockIdx.x % L.nchunk;
+    const int jb = blockIdx.x / L.nchunk;
+    const int s = chunk * 32 + threadIdx.x;
+    RowPos rp;
+    rp.j = jb * 8 + threadIdx.y;
+    rp.k = blockIdx.y;
+    rp.l = blockIdx.z;
+    if (rp.j >= L.n2 || s >= L.P) return;
+    rp.p = (rp.j + rp.k + rp.l) & 1;
+    if (2 * s + (C ^ rp.p) >= L.n1) return;
+    const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
+    const long long q = (long long)row * L.P + s;
+    const float *dother = d + (C ? 0 : L.S);
+    float *dself = d + (C ? L.S : 0);
+    const float acc = neighbour_sum<C, false, __nv_bfloat16>(L, dother, Wb, row, s, rp);
+    const float dbar = rho[C * L.S + q] + gb[C * L.S + q] * acc;
+    const float d0 = dself[q];
+    dself[q] = d0 + omega * (dbar - d0);
+}
+
+// u <- u + delta over both colour halves (padding holds 0 in both)
+__global__ void __launch_bounds__(256) k_apply(float4 *__restrict__ u,
+                                               const float4 *__restrict__ delta, long long n4)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        float4 a = u[i];
+        const float4 b = delta[i];
+        a.x += b.x;
+        a.y += b.y;
+        a.z += b.z;
+        a.w += b.w;
+        u[i] = a;
+    }
+}
+
+void launch_mixed_prepare(const Layout &L, const float *W, const float *gamma, const float *diag,
+                          void *Wb, float *gb, float *ib, cudaStream_t st)
+{
+    k_mixed_prepare<<<kPartBlocks, 256, 0, st>>>(L, W, gamma, diag, (__nv_bfloat16 *)Wb, gb, ib);
+}
+
+void launch_defect(const Layout &L, const float *u, const float *beta, const float *gamma,
+                   const float *diag, const float *W, const float *ib, float *rho, float *delta,
+                   double *partials, int nparts, cudaStream_t st)
+{
+    k_defect<<<nparts, kPartThreads, 0, st>>>(L, u, beta, gamma, diag, W, ib, rho, delta,
+                                              partials);
+}
+
+void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *rho,
+                        const float *gb, const void *Wb, float omega, cudaStream_t st)
+{
+    dim3 block(32, 8);
+    dim3 grid((unsigned)(L.nchunk * L.njb), (unsigned)L.n3, (unsigned)L.n4);
+    const __nv_bfloat16 *w = (const __nv_bfloat16 *)Wb;
+    if (colour == 0)
+        k_sweep_mixed<0><<<grid, block, 0, st>>>(L, delta, rho, gb, w, omega);
+    else
+        k_sweep_mixed<1><<<grid, block, 0, st>>>(L, delta, rho, gb, w, omega);
+}
+
+void launch_apply(const Layout &L, float *u, const float *delta, cudaStream_t st)
+{
+    // 2S floats; P is a multiple of 4, so 2S is too and the halves are 16-byte aligned
+    const long long n4 = 2 * L.S / 4;
+    long long blocks = (n4 + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    k_apply<<<(int)(blocks < 1 ? 1 : blocks), 256, 0, st>>>((float4 *)u, (const float4 *)delta,
+                                                            n4);
+}
+
+}  // namespace seg4d_impl

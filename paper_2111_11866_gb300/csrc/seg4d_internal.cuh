@@ -125,6 +125,15 @@ void launch_sweep(const Layout &L, int colour, float *x, const float *beta, cons
 void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta,
                        const float *gamma, const float *W, float omega, unsigned *ctrl, int ctas,
                        int test_wait, cudaStream_t st);
+// mixed precision (mixed_kernels.cu); Wb is a __nv_bfloat16 [8][S] array
+void launch_mixed_prepare(const Layout &L, const float *W, const float *gamma, const float *diag,
+                          void *Wb, float *gb, float *ib, cudaStream_t st);
+void launch_defect(const Layout &L, const float *u, const float *beta, const float *gamma,
+                   const float *diag, const float *W, const float *ib, float *rho, float *delta,
+                   double *partials, int nparts, cudaStream_t st);
+void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *rho,
+                        const float *gb, const void *Wb, float omega, cudaStream_t st);
+void launch_apply(const Layout &L, float *u, const float *delta, cudaStream_t st);
 int wave_tiles(const Layout &L);        // tiles per frame of the fused sweep
 int wave_max_ctas_per_sm();             // occupancy limit of the fused sweep
 void launch_residual(const Layout &L, const float *x, const float *beta, const float *gamma,

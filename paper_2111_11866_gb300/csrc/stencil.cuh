@@ -8,6 +8,8 @@
 #include <cfloat>
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "seg4d_internal.cuh"
 
 namespace seg4d_impl {
@@ -72,9 +74,13 @@ __device__ __forceinline__ float ldu(const float *p)
     return kCG ? __ldcg(p) : *p;
 }
 
-template <int C, bool kCG = false>
+// face weight load: FP32, or BF16 widened to FP32
+__device__ __forceinline__ float ldw(const float *p) { return *p; }
+__device__ __forceinline__ float ldw(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+template <int C, bool kCG = false, typename WT = float>
 __device__ __forceinline__ float neighbour_sum(const Layout &L, const float *__restrict__ xo,
-                                               const float *__restrict__ W, int row, int s,
+                                               const WT *__restrict__ W, int row, int s,
                                                const RowPos &rp)
 {
     const long long S = L.S;
@@ -86,24 +92,24 @@ __device__ __forceinline__ float neighbour_sum(const Layout &L, const float *__r
     float t0, t1, t2, t3, t4, t5, t6, t7;
     if (C == 0) {
         const int sxm = s - 1 + rp.p, sxp = s + rp.p;
-        t0 = sxm >= 0 ? W[0 * S + q] * ldu<kCG>(xo + rb + sxm) : 0.0f;
-        t1 = sxp < L.P ? W[1 * S + q] * ldu<kCG>(xo + rb + sxp) : 0.0f;
-        t2 = rp.j > 0 ? W[2 * S + q] * ldu<kCG>(xo + q - dy) : 0.0f;
-        t3 = rp.j + 1 < L.n2 ? W[3 * S + q] * ldu<kCG>(xo + q + dy) : 0.0f;
-        t4 = rp.k > 0 ? W[4 * S + q] * ldu<kCG>(xo + q - dz) : 0.0f;
-        t5 = rp.k + 1 < L.n3 ? W[5 * S + q] * ldu<kCG>(xo + q + dz) : 0.0f;
-        t6 = rp.l > 0 ? W[6 * S + q] * ldu<kCG>(xo + q - dt) : 0.0f;
-        t7 = rp.l + 1 < L.n4 ? W[7 * S + q] * ldu<kCG>(xo + q + dt) : 0.0f;
+        t0 = sxm >= 0 ? ldw(W + 0 * S + q) * ldu<kCG>(xo + rb + sxm) : 0.0f;
+        t1 = sxp < L.P ? ldw(W + 1 * S + q) * ldu<kCG>(xo + rb + sxp) : 0.0f;
+        t2 = rp.j > 0 ? ldw(W + 2 * S + q) * ldu<kCG>(xo + q - dy) : 0.0f;
+        t3 = rp.j + 1 < L.n2 ? ldw(W + 3 * S + q) * ldu<kCG>(xo + q + dy) : 0.0f;
+        t4 = rp.k > 0 ? ldw(W + 4 * S + q) * ldu<kCG>(xo + q - dz) : 0.0f;
+        t5 = rp.k + 1 < L.n3 ? ldw(W + 5 * S + q) * ldu<kCG>(xo + q + dz) : 0.0f;
+        t6 = rp.l > 0 ? ldw(W + 6 * S + q) * ldu<kCG>(xo + q - dt) : 0.0f;
+        t7 = rp.l + 1 < L.n4 ? ldw(W + 7 * S + q) * ldu<kCG>(xo + q + dt) : 0.0f;
     } else {
         const int sxm = s - rp.p, sxp = s + 1 - rp.p;
-        t0 = sxm >= 0 ? W[1 * S + rb + sxm] * ldu<kCG>(xo + rb + sxm) : 0.0f;
-        t1 = sxp < L.P ? W[0 * S + rb + sxp] * ldu<kCG>(xo + rb + sxp) : 0.0f;
-        t2 = rp.j > 0 ? W[3 * S + q - dy] * ldu<kCG>(xo + q - dy) : 0.0f;
-        t3 = rp.j + 1 < L.n2 ? W[2 * S + q + dy] * ldu<kCG>(xo + q + dy) : 0.0f;
-        t4 = rp.k > 0 ? W[5 * S + q - dz] * ldu<kCG>(xo + q - dz) : 0.0f;
-        t5 = rp.k + 1 < L.n3 ? W[4 * S + q + dz] * ldu<kCG>(xo + q + dz) : 0.0f;
-        t6 = rp.l > 0 ? W[7 * S + q - dt] * ldu<kCG>(xo + q - dt) : 0.0f;
-        t7 = rp.l + 1 < L.n4 ? W[6 * S + q + dt] * ldu<kCG>(xo + q + dt) : 0.0f;
+        t0 = sxm >= 0 ? ldw(W + 1 * S + rb + sxm) * ldu<kCG>(xo + rb + sxm) : 0.0f;
+        t1 = sxp < L.P ? ldw(W + 0 * S + rb + sxp) * ldu<kCG>(xo + rb + sxp) : 0.0f;
+        t2 = rp.j > 0 ? ldw(W + 3 * S + q - dy) * ldu<kCG>(xo + q - dy) : 0.0f;
+        t3 = rp.j + 1 < L.n2 ? ldw(W + 2 * S + q + dy) * ldu<kCG>(xo + q + dy) : 0.0f;
+        t4 = rp.k > 0 ? ldw(W + 5 * S + q - dz) * ldu<kCG>(xo + q - dz) : 0.0f;
+        t5 = rp.k + 1 < L.n3 ? ldw(W + 4 * S + q + dz) * ldu<kCG>(xo + q + dz) : 0.0f;
+        t6 = rp.l > 0 ? ldw(W + 7 * S + q - dt) * ldu<kCG>(xo + q - dt) : 0.0f;
+        t7 = rp.l + 1 < L.n4 ? ldw(W + 6 * S + q + dt) * ldu<kCG>(xo + q + dt) : 0.0f;
     }
     return ((t0 + t1) + (t2 + t3)) + ((t4 + t5) + (t6 + t7));
 }
@@ -173,5 +179,50 @@ __device__ inline void face_grad_sq8(const Layout &L, const float *__restrict__ 
     }
 }
 
+
+// Sum over the interior faces of (w_f - bf16(w_f)) for the voxel in slot s
+// (red voxels own their weights, black voxels read them across the face).
+template <int C>
+__device__ __forceinline__ float rounding_excess(const Layout &L, const float *__restrict__ W,
+                                                 int row, int s, const RowPos &rp)
+{
+    const long long S = L.S;
+    const long long rb = (long long)row * L.P;
+    const long long q = rb + s;
+    const long long dy = L.P, dz = (long long)L.n2 * L.P, dt = (long long)L.n2 * L.n3 * L.P;
+    long long idx[8];
+    bool in[8];
+    if (C == 0) {
+        in[0] = s - 1 + rp.p >= 0 && 2 * s + rp.p >= 1;
+        in[1] = 2 * s + rp.p + 1 < L.n1;
+        for (int f = 0; f < 8; ++f) idx[f] = (long long)f * S + q;
+    } else {
+        const int i = 2 * s + 1 - rp.p;
+        in[0] = i >= 1;
+        in[1] = i + 1 < L.n1;
+        idx[0] = 1 * S + rb + s - rp.p;
+        idx[1] = 0 * S + rb + s + 1 - rp.p;
+        idx[2] = 3 * S + q - dy;
+        idx[3] = 2 * S + q + dy;
+        idx[4] = 5 * S + q - dz;
+        idx[5] = 4 * S + q + dz;
+        idx[6] = 7 * S + q - dt;
+        idx[7] = 6 * S + q + dt;
+    }
+    in[2] = rp.j > 0;
+    in[3] = rp.j + 1 < L.n2;
+    in[4] = rp.k > 0;
+    in[5] = rp.k + 1 < L.n3;
+    in[6] = rp.l > 0;
+    in[7] = rp.l + 1 < L.n4;
+    float ex = 0.0f;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+        if (!in[f]) continue;
+        const float w = W[idx[f]];
+        ex += w - __bfloat162float(__float2bfloat16_rn(w));
+    }
+    return ex;
+}
 
 }  // namespace seg4d_impl

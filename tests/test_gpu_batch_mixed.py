@@ -1,0 +1,69 @@
+"""Batched windows in mixed precision: BF16 face weights in the batched sweeps,
+exact FP32 defect passes; same parity bar against the oracle, same
+alone-vs-mix bit equality as the FP32 batch."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2111_11866_gb300 import _lib, synth
+
+from gpu_common import REL_TOL, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2111_11866_gb300 import build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _params(precision):
+    p = _lib.Params.defaults()
+    p.r_ball = p.R_init = 6.0
+    p.precision = precision
+    return p
+
+
+def _specs():
+    out = {}
+    for k, (seed, n) in enumerate([(201, (37, 29, 17, 5)), (202, (24, 24, 24, 4))]):
+        c = synth.small_nuclei(seed=seed, n=n, count=2, nsteps=3)
+        out[k] = (c.image, c.seeds, 3)
+    return out
+
+
+def _run(specs, p):
+    res = {}
+    with _lib.Batch(1 << 30, 16, params=p) as b:
+        ids = {k: b.add(*v) for k, v in specs.items()}
+        for _ in range(3):
+            b.advance()
+        for k, wid in ids.items():
+            assert b.poll(wid)["state"] == "done"
+            res[k] = b.read_u(wid)
+    return res
+
+
+def test_mixed_batch_matches_oracle_and_is_mix_independent():
+    specs = _specs()
+    p = _params(1)
+    mix = _run(specs, p)
+    P = oracle_params(p)
+    for k, (img, seeds, nsteps) in specs.items():
+        ref, _ = O.segment(img.astype(np.float64), seeds, P, nsteps=nsteps)
+        assert np.abs(mix[k] - ref).max() <= REL_TOL * np.abs(ref).max()
+        alone = _run({k: specs[k]}, p)
+        np.testing.assert_array_equal(alone[k], mix[k])
+
+
+def test_precision_fixed_while_windows_resident():
+    specs = _specs()
+    with _lib.Batch(1 << 30, 4, params=_params(0)) as b:
+        b.add(*specs[0])
+        with pytest.raises(_lib.Seg4DError):
+            b.set_params(precision=1)
+    assert _lib.Batch.window_bytes((24, 24, 24, 4), 1, 1) > _lib.Batch.window_bytes((24, 24, 24, 4))
