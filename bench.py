@@ -36,8 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # capture of the current kernel (profiles/); None after a kernel changes until
 # it is captured again.
 SWEEP_KERNELS = {0: "k_sweep_wave (fused red-black wavefront, several sweeps per launch)",
-                 1: "k_sweep (one colour of a red-black sweep per launch)"}
-SWEEP_TRAFFIC_PER_SWEEP = {0: None, 1: 2 * 860.8e6}
+                 1: "k_sweep_vec (one colour of a red-black sweep per launch, 2 voxels/thread)"}
+SWEEP_TRAFFIC_PER_SWEEP = {0: None, 1: None}
 
 
 def _env_int(name, default):

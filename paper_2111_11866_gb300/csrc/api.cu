@@ -41,7 +41,7 @@ struct seg4d {
     float *I0 = nullptr, *ITH = nullptr, *Is0 = nullptr, *IsTH = nullptr;
     int *owner = nullptr;
     float *stage = nullptr;        // natural-layout staging, n1*n2*n3*n4 floats
-    double *partials = nullptr;    // 3 * kPartBlocks doubles (scratch)
+    double *partials = nullptr;    // 3 * kPartCap doubles (scratch)
     double *scal = nullptr;        // 8 doubles: reduced records
     double *host_scal = nullptr;   // pinned mirror of scal
     unsigned *wave_ctrl = nullptr; // fused-sweep control block: 4 + tiles u32
@@ -134,7 +134,7 @@ size_t bytes_for(const Layout &L, long long nv)
     b += 2 * S * sizeof(float) * 4;        // I0, ITH, Is0, IsTH
     b += 2 * S * sizeof(int);              // owner
     b += (size_t)nv * sizeof(float);       // staging
-    b += 3 * kPartBlocks * sizeof(double) + 8 * sizeof(double);
+    b += 3 * kPartCap * sizeof(double) + 8 * sizeof(double);
     return b;
 }
 
@@ -184,9 +184,9 @@ seg4d_status use_device(seg4d *h)
 }
 
 // reduce the per-block records into scal[slot..slot+2]
-seg4d_status reduce_into(seg4d *h, int slot)
+seg4d_status reduce_into(seg4d *h, int slot, int nrec = kPartBlocks)
 {
-    launch_reduce_partials(h->partials, kPartBlocks, h->scal + slot, h->stream);
+    launch_reduce_partials(h->partials, nrec, h->scal + slot, h->stream);
     h->launches += 1;
     CK_LAUNCH("reduce");
     return SEG4D_OK;
@@ -222,23 +222,31 @@ seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_
     int it = 0;
     bool timed_batch = false;
     // Checks are spaced by a prediction from the observed contraction: after
-    // two checks with r_now < r_prev, rho = (r_now/r_prev)^(1/sweeps) and the
-    // next check comes after log(tol*||b|| / r_now) / log(rho) sweeps, kept in
-    // [max(1, check_every/4), 8*check_every].  The first batch is check_every.
+    // two checks with r_now < r_prev, rho = (r_now/r_prev)^(1/sweeps) and
+    // need = log(tol*||b|| / r_now) / log(rho) sweeps remain.  SOR contracts
+    // faster as it proceeds, so need over-estimates: the next batch is
+    // 0.8 * need, and at most the sweeps that cut the residual by the factor
+    // `gain` at rate rho, so that rho is re-measured on the way.  A mixed
+    // cycle cannot gain much more than the inverse of the BF16 weight error
+    // (about 2^9) before the correction system's own error dominates, so
+    // mixed cycles aim at 1e-2, plain batches at 1e-3.  Batches are kept in
+    // [max(1, check_every/4), 8*check_every]; the first is check_every.
+    const double gain = mixed ? 1e-2 : 1e-3;
     int batch = check_every;
     double prev_rn = -1.0;
     int prev_it = 0;
     bool wave_pending = false;
     for (;;) {
+        int nrec = kPartBlocks;
         if (mixed)
             launch_defect(L, x, h->beta, h->gamma, h->diag, h->W, h->ib, h->rho, h->dlt,
                           h->partials, kPartBlocks, h->stream);
         else
-            launch_residual(L, x, h->beta, h->gamma, h->diag, h->W, h->partials, kPartBlocks,
-                            h->stream);
+            nrec = launch_residual(L, x, h->beta, h->gamma, h->diag, h->W, h->partials,
+                                   h->stream);
         h->launches += 1;
         CK_LAUNCH("residual");
-        if ((st = reduce_into(h, 3))) return st;   // scal[3..5] = sum r^2, min u, max u
+        if ((st = reduce_into(h, 3, nrec))) return st;   // scal[3..5] = sum r^2, min u, max u
         if ((st = fetch_scal(h))) return st;
         if (wave_pending) {
             wave_pending = false;
@@ -268,8 +276,10 @@ seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_
         if (prev_rn > 0.0 && rn < prev_rn && it > prev_it && rn > 0.0) {
             const double rho = std::pow(rn / prev_rn, 1.0 / (it - prev_it));
             const double need = std::log(tol * bn / rn) / std::log(rho);
+            const double cap = std::log(gain) / std::log(rho);
             const int lo = std::max(1, check_every / 4), hi = 8 * check_every;
-            batch = std::isfinite(need) ? (int)std::min<double>(hi, std::max<double>(lo, std::ceil(need)))
+            const double want = std::ceil(std::min(0.8 * need, cap));
+            batch = std::isfinite(want) ? (int)std::min<double>(hi, std::max<double>(lo, want))
                                         : check_every;
         } else {
             batch = check_every;
@@ -474,7 +484,8 @@ seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
             CK(cudaMemsetAsync(h->dlt, 0, S2 * sizeof(float), h->stream));
             CK(cudaMemsetAsync(h->Wb, 0, 4 * S2 * sizeof(unsigned short), h->stream));
         }
-        launch_mixed_prepare(h->L, h->W, h->gamma, h->diag, h->Wb, h->gb, h->ib, h->stream);
+        launch_mixed_prepare(h->L, h->u, h->W, h->gamma, h->diag, h->Wb, h->gb, h->ib, h->beta,
+                             h->stream);
         h->launches += 1;
         CK_LAUNCH("mixed_prepare");
     }
@@ -617,7 +628,7 @@ seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out
         {(void **)&h->I0, 2 * S * 4},    {(void **)&h->ITH, 2 * S * 4},
         {(void **)&h->Is0, 2 * S * 4},   {(void **)&h->IsTH, 2 * S * 4},
         {(void **)&h->owner, 2 * S * 4}, {(void **)&h->stage, (size_t)nv * 4},
-        {(void **)&h->partials, 3 * kPartBlocks * sizeof(double)},
+        {(void **)&h->partials, 3 * kPartCap * sizeof(double)},
         {(void **)&h->scal, 8 * sizeof(double)},
         {(void **)&h->wave_ctrl, (4 + (size_t)wave_tiles(L)) * sizeof(unsigned)},
     };

@@ -103,29 +103,55 @@ __device__ inline bool tile_pos(const BWin &wd, long long t, RowPos &rp, int &s,
     return true;
 }
 
+// Sweeps take N slots per thread (N = kVecF32, or kVecBF16 in mixed
+// precision): the groups (row, s0), s0 a multiple of N, of one colour are
+// enumerated as e = (row * P + s0) / N and cut into tiles of 256.
+__host__ __device__ inline long long win_gtiles(const Layout &L, int N)
+{
+    return (L.S / N + 255) / 256;
+}
+
+// group tile t of window wd -> thread's (row position, s0); false past the end
+template <int N>
+__device__ inline bool group_pos(const BWin &wd, long long t, RowPos &rp, int &s0, int &row)
+{
+    const long long e = t * 256 + threadIdx.x;
+    if (N * e >= wd.L.S) return false;
+    const unsigned ue = (unsigned)(N * e);
+    const unsigned r = fdiv(ue, wd.fP);
+    s0 = (int)(ue - r * (unsigned)wd.L.P);
+    const unsigned a = fdiv(r, wd.fn2);
+    rp.j = (int)(r - a * (unsigned)wd.L.n2);
+    const unsigned c = fdiv(a, wd.fn3);
+    rp.k = (int)(a - c * (unsigned)wd.L.n3);
+    rp.l = (int)c;
+    rp.p = (rp.j + rp.k + rp.l) & 1;
+    row = (int)r;
+    return true;
+}
+
 // --------------------------------------------------------------- kernels
 
-template <int C>
-__global__ void __launch_bounds__(256, 8) k_bsweep(const BWin *__restrict__ wins,
-                                                   const long long *__restrict__ starts, int nwin,
-                                                   float omega)
+// One colour of one sweep over every window, N voxels per thread
+// (relax_vec); mixed windows sweep the BF16 correction system instead.  The
+// black pass takes the tiles in reverse, starting on what is still in L2.
+template <int C, bool kMixed, int N = kMixed ? kVecBF16 : kVecF32>
+__global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_bsweep(
+    const BWin *__restrict__ wins, const long long *__restrict__ starts, int nwin, float omega)
 {
-    const long long b = blockIdx.x;
+    const long long b = C ? (long long)gridDim.x - 1 - blockIdx.x : blockIdx.x;
     const int w = find_win(starts, nwin, b);
     const Layout L = wins[w].L;
-    RowPos rp;
-    int s, row;
-    if (!tile_pos(wins[w], b - starts[w], rp, s, row)) return;
-    if (2 * s + (C ^ rp.p) >= L.n1) return;
-    float *x = wins[w].x;
-    const float *beta = wins[w].beta, *gamma = wins[w].gamma, *W = wins[w].W;
-    const long long q = (long long)row * L.P + s;
-    const float *xo = x + (C ? 0 : L.S);
-    float *xs = x + (C ? L.S : 0);
-    const float acc = neighbour_sum<C>(L, xo, W, row, s, rp);
-    const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
-    const float u0 = xs[q];
-    xs[q] = u0 + omega * (ubar - u0);
+    RowPos rp{0, 0, 0, 0};
+    int s0 = 0, row = 0;
+    bool act = group_pos<N>(wins[w], b - starts[w], rp, s0, row);
+    act = act && 2 * s0 + (C ^ rp.p) < L.n1;
+    if (kMixed)
+        relax_vec<C, __nv_bfloat16, N>(L, wins[w].dlt, wins[w].rho, wins[w].gb, wins[w].Wb, omega,
+                                       act, row, s0, rp);
+    else
+        relax_vec<C, float, N>(L, wins[w].x, wins[w].beta, wins[w].gamma, wins[w].W, omega, act,
+                               row, s0, rp);
 }
 
 // residual records per chunk of kChunkTiles tiles: (sum r^2, min x, max x)
@@ -140,7 +166,7 @@ __global__ void __launch_bounds__(256) k_bresidual(const BWin *__restrict__ wins
     const float *diag = wins[w].diag, *W = wins[w].W;
     const long long nt = win_tiles(L);
     const long long t0 = (b - cstarts[w]) * kChunkTiles;
-    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    Rec3f a = rec3f_init();
     for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
         RowPos rp;
         int s, row;
@@ -151,14 +177,12 @@ __global__ void __launch_bounds__(256) k_bresidual(const BWin *__restrict__ wins
             const float acc = C ? neighbour_sum<1>(L, x, W, row, s, rp)
                                 : neighbour_sum<0>(L, x + L.S, W, row, s, rp);
             const float u = x[C * L.S + q];
-            const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
-            const double r = (double)diag[C * L.S + q] * ((double)ubar - (double)u);
-            a.sum += r * r;
-            a.mn = fmin(a.mn, (double)u);
-            a.mx = fmax(a.mx, (double)u);
+            const float ubar = __fmaf_rn(gamma[C * L.S + q], acc, beta[C * L.S + q]);
+            const float r = __fmul_rn(diag[C * L.S + q], __fsub_rn(ubar, u));
+            rec3f_add(a, __fmul_rn(r, r), u);
         }
     }
-    block_write3(a, parts + 3 * b);
+    block_write3(rec3f_acc(a), parts + 3 * b);
 }
 
 // per-window fixed-order reduction of the chunk records (one block per window)
@@ -185,7 +209,7 @@ __global__ void __launch_bounds__(256) k_bcoef(const BWin *__restrict__ wins,
     float *beta = wins[w].beta, *gamma = wins[w].gamma, *diag = wins[w].diag, *W = wins[w].W;
     const long long nt = win_tiles(L);
     const long long t0 = (b - cstarts[w]) * kChunkTiles;
-    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    Rec3f a = rec3f_init();
     for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
         RowPos rp;
         int s, row;
@@ -214,12 +238,10 @@ __global__ void __launch_bounds__(256) k_bcoef(const BWin *__restrict__ wins,
             diag[C * L.S + q] = D;
             beta[C * L.S + q] = bv / D;
             gamma[C * L.S + q] = cc / D;
-            a.sum += (double)bv * (double)bv;
-            a.mn = fmin(a.mn, (double)bv);
-            a.mx = fmax(a.mx, (double)bv);
+            rec3f_add(a, __fmul_rn(bv, bv), bv);
         }
     }
-    block_write3(a, parts + 3 * b);
+    block_write3(rec3f_acc(a), parts + 3 * b);
 }
 
 // presmoothing coefficients for every window's x (one implicit heat step,
@@ -238,7 +260,7 @@ __global__ void __launch_bounds__(256) k_bsmooth_coef(const BWin *__restrict__ w
     const int nn[4] = {L.n1, L.n2, L.n3, L.n4};
     const long long nt = win_tiles(L);
     const long long t0 = (b - cstarts[w]) * kChunkTiles;
-    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    Rec3f a = rec3f_init();
     for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
         RowPos rp;
         int s, row;
@@ -261,12 +283,10 @@ __global__ void __launch_bounds__(256) k_bsmooth_coef(const BWin *__restrict__ w
             diag[C * L.S + q] = D;
             beta[C * L.S + q] = bv / D;
             gamma[C * L.S + q] = sigma_t / D;
-            a.sum += (double)bv * (double)bv;
-            a.mn = fmin(a.mn, (double)bv);
-            a.mx = fmax(a.mx, (double)bv);
+            rec3f_add(a, __fmul_rn(bv, bv), bv);
         }
     }
-    block_write3(a, parts + 3 * b);
+    block_write3(rec3f_acc(a), parts + 3 * b);
 }
 
 // ---- mixed precision (see mixed_kernels.cu for the scheme)
@@ -280,8 +300,9 @@ __global__ void __launch_bounds__(256) k_bmixed_prepare(const BWin *__restrict__
     if (!wins[w].mixed) return;
     const Layout L = wins[w].L;
     const float *W = wins[w].W, *gamma = wins[w].gamma, *diag = wins[w].diag;
+    const float *u = wins[w].u;
     __nv_bfloat16 *Wb = wins[w].Wb;
-    float *gb = wins[w].gb, *ib = wins[w].ib;
+    float *gb = wins[w].gb, *ib = wins[w].ib, *beta = wins[w].beta;
     const long long nt = win_tiles(L);
     const long long t0 = (b - cstarts[w]) * kChunkTiles;
     for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
@@ -298,6 +319,7 @@ __global__ void __launch_bounds__(256) k_bmixed_prepare(const BWin *__restrict__
             const float Db = D - c * ex;
             gb[C * L.S + q] = c / Db;
             ib[C * L.S + q] = 1.0f / Db;
+            beta[C * L.S + q] = u[C * L.S + q];
             if (C == 0)
                 for (int f = 0; f < 8; ++f)
                     Wb[(long long)f * L.S + q] = __float2bfloat16_rn(W[(long long)f * L.S + q]);
@@ -305,7 +327,8 @@ __global__ void __launch_bounds__(256) k_bmixed_prepare(const BWin *__restrict__
     }
 }
 
-// exact residual (records) + rho = r / D_b, delta = 0
+// exact residual in flux form (records) + rho = r / D_b, delta = 0; beta
+// holds b itself after k_bmixed_prepare
 __global__ void __launch_bounds__(256) k_bdefect(const BWin *__restrict__ wins,
                                                  const long long *__restrict__ cstarts, int nwin,
                                                  double *__restrict__ parts)
@@ -318,7 +341,7 @@ __global__ void __launch_bounds__(256) k_bdefect(const BWin *__restrict__ wins,
     float *rho = wins[w].rho, *dlt = wins[w].dlt;
     const long long nt = win_tiles(L);
     const long long t0 = (b - cstarts[w]) * kChunkTiles;
-    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    Rec3f a = rec3f_init();
     for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
         RowPos rp;
         int s, row;
@@ -326,44 +349,15 @@ __global__ void __launch_bounds__(256) k_bdefect(const BWin *__restrict__ wins,
         const long long q = (long long)row * L.P + s;
         for (int C = 0; C < 2; ++C) {
             if (2 * s + (C ^ rp.p) >= L.n1) continue;
-            const float acc = C ? neighbour_sum<1>(L, x, W, row, s, rp)
-                                : neighbour_sum<0>(L, x + L.S, W, row, s, rp);
-            const float u = x[C * L.S + q];
-            const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
-            const float r = diag[C * L.S + q] * (ubar - u);
+            float u;
+            const float r = C ? flux_residual<1>(L, x, beta, gamma, diag, W, row, s, rp, u)
+                              : flux_residual<0>(L, x, beta, gamma, diag, W, row, s, rp, u);
             rho[C * L.S + q] = r * ib[C * L.S + q];
             dlt[C * L.S + q] = 0.0f;
-            const double rd = (double)diag[C * L.S + q] * ((double)ubar - (double)u);
-            a.sum += rd * rd;
-            a.mn = fmin(a.mn, (double)u);
-            a.mx = fmax(a.mx, (double)u);
+            rec3f_add(a, __fmul_rn(r, r), u);
         }
     }
-    block_write3(a, parts + 3 * b);
-}
-
-template <int C>
-__global__ void __launch_bounds__(256, 8) k_bsweep_mixed(const BWin *__restrict__ wins,
-                                                         const long long *__restrict__ starts,
-                                                         int nwin, float omega)
-{
-    const long long b = blockIdx.x;
-    const int w = find_win(starts, nwin, b);
-    const Layout L = wins[w].L;
-    RowPos rp;
-    int s, row;
-    if (!tile_pos(wins[w], b - starts[w], rp, s, row)) return;
-    if (2 * s + (C ^ rp.p) >= L.n1) return;
-    float *d = wins[w].dlt;
-    const float *rho = wins[w].rho, *gb = wins[w].gb;
-    const __nv_bfloat16 *Wb = wins[w].Wb;
-    const long long q = (long long)row * L.P + s;
-    const float *dother = d + (C ? 0 : L.S);
-    float *dself = d + (C ? L.S : 0);
-    const float acc = neighbour_sum<C, false, __nv_bfloat16>(L, dother, Wb, row, s, rp);
-    const float dbar = rho[C * L.S + q] + gb[C * L.S + q] * acc;
-    const float d0 = dself[q];
-    dself[q] = d0 + omega * (dbar - d0);
+    block_write3(rec3f_acc(a), parts + 3 * b);
 }
 
 // x <- x + delta on every slot of the tile (padding holds 0 in both)
@@ -573,12 +567,13 @@ struct seg4d_batch {
     // pinned host copies are not rewritten before their last upload has run
     BWin *d_wins = nullptr, *h_wins = nullptr;
     long long *d_chunk = nullptr, *h_chunk = nullptr;   // reduction chunks
-    long long *d_tile = nullptr, *h_tile = nullptr;     // sweep tiles
+    long long *d_tile = nullptr, *h_tile = nullptr;     // 256-slot tiles
+    long long *d_ptile = nullptr, *h_ptile = nullptr;   // sweep tiles of 256 N-slot groups
     long long *d_seed = nullptr, *h_seed = nullptr;     // seed blocks
     cudaEvent_t ev_table = nullptr;
     bool table_pending = false;
     std::vector<std::pair<int, float *>> table_key;     // (window id, x) uploaded
-    long long n_chunk = 0, n_tile = 0, n_seed = 0;
+    long long n_chunk = 0, n_tile = 0, n_ptile = 0, n_seed = 0;
     double *d_out = nullptr, *h_out = nullptr;
     double *d_parts = nullptr;
     size_t parts_cap = 0;    // chunk records
@@ -689,28 +684,34 @@ seg4d_status set_table(seg4d_batch *b, const std::vector<Window *> &ws)
         BCK(cudaEventSynchronize(b->ev_table));
         b->table_pending = false;
     }
-    long long c = 0, t = 0, sd = 0;
+    long long c = 0, t = 0, pt = 0, sd = 0;
     for (size_t i = 0; i < ws.size(); ++i) {
         b->h_wins[i] = ws[i]->d;
         b->h_chunk[i] = c;
         b->h_tile[i] = t;
+        b->h_ptile[i] = pt;
         b->h_seed[i] = sd;
         c += chunks_of(*ws[i]);
         t += win_tiles(ws[i]->L);
+        pt += win_gtiles(ws[i]->L, b->p.precision == 1 ? kVecBF16 : kVecF32);
         sd += ws[i]->d.nseeds;
     }
     const size_t n = ws.size();
     b->h_chunk[n] = c;
     b->h_tile[n] = t;
+    b->h_ptile[n] = pt;
     b->h_seed[n] = sd;
     b->n_chunk = c;
     b->n_tile = t;
+    b->n_ptile = pt;
     b->n_seed = sd;
     BCK(cudaMemcpyAsync(b->d_wins, b->h_wins, sizeof(BWin) * n, cudaMemcpyHostToDevice, b->stream));
     BCK(cudaMemcpyAsync(b->d_chunk, b->h_chunk, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
                         b->stream));
     BCK(cudaMemcpyAsync(b->d_tile, b->h_tile, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
                         b->stream));
+    BCK(cudaMemcpyAsync(b->d_ptile, b->h_ptile, sizeof(long long) * (n + 1),
+                        cudaMemcpyHostToDevice, b->stream));
     BCK(cudaMemcpyAsync(b->d_seed, b->h_seed, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
                         b->stream));
     BCK(cudaEventRecord(b->ev_table, b->stream));
@@ -823,17 +824,19 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
         const long long ntiles = b->n_tile;
         const int n = std::min(check_every, max_iters - it);
         BCK(cudaEventRecord(b->e0, b->stream));
+        const long long nptiles = b->n_ptile;
+        const int nw = (int)ws.size();
         for (int s = 0; s < n; ++s) {
             if (mixed) {
-                k_bsweep_mixed<0><<<(unsigned)ntiles, 256, 0, b->stream>>>(
-                    b->d_wins, b->d_tile, (int)ws.size(), (float)omega);
-                k_bsweep_mixed<1><<<(unsigned)ntiles, 256, 0, b->stream>>>(
-                    b->d_wins, b->d_tile, (int)ws.size(), (float)omega);
+                k_bsweep<0, true><<<(unsigned)nptiles, 256, 0, b->stream>>>(b->d_wins, b->d_ptile,
+                                                                            nw, (float)omega);
+                k_bsweep<1, true><<<(unsigned)nptiles, 256, 0, b->stream>>>(b->d_wins, b->d_ptile,
+                                                                            nw, (float)omega);
             } else {
-                k_bsweep<0><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
-                                                                     (int)ws.size(), (float)omega);
-                k_bsweep<1><<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
-                                                                     (int)ws.size(), (float)omega);
+                k_bsweep<0, false><<<(unsigned)nptiles, 256, 0, b->stream>>>(
+                    b->d_wins, b->d_ptile, nw, (float)omega);
+                k_bsweep<1, false><<<(unsigned)nptiles, 256, 0, b->stream>>>(
+                    b->d_wins, b->d_ptile, nw, (float)omega);
             }
         }
         if (mixed) {
@@ -1038,12 +1041,14 @@ void batch_free(seg4d_batch *b)
     cudaFree(b->d_wins);
     cudaFree(b->d_chunk);
     cudaFree(b->d_tile);
+    cudaFree(b->d_ptile);
     cudaFree(b->d_seed);
     cudaFree(b->d_out);
     cudaFree(b->d_parts);
     if (b->h_wins) cudaFreeHost(b->h_wins);
     if (b->h_chunk) cudaFreeHost(b->h_chunk);
     if (b->h_tile) cudaFreeHost(b->h_tile);
+    if (b->h_ptile) cudaFreeHost(b->h_ptile);
     if (b->h_seed) cudaFreeHost(b->h_seed);
     if (b->ev_table) cudaEventDestroy(b->ev_table);
     if (b->h_out) cudaFreeHost(b->h_out);
@@ -1077,11 +1082,13 @@ seg4d_status seg4d_batch_create(size_t arena_bytes, int max_windows, void *cuda_
               cudaMalloc(&b->d_wins, sizeof(BWin) * max_windows) == cudaSuccess &&
               cudaMalloc(&b->d_chunk, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMalloc(&b->d_tile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaMalloc(&b->d_ptile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMalloc(&b->d_seed, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMalloc(&b->d_out, 3 * sizeof(double) * max_windows) == cudaSuccess &&
               cudaMallocHost(&b->h_wins, sizeof(BWin) * max_windows) == cudaSuccess &&
               cudaMallocHost(&b->h_chunk, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMallocHost(&b->h_tile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
+              cudaMallocHost(&b->h_ptile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMallocHost(&b->h_seed, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaEventCreate(&b->ev_table) == cudaSuccess &&
               cudaMallocHost(&b->h_out, 3 * sizeof(double) * max_windows) == cudaSuccess &&

@@ -38,14 +38,18 @@ namespace seg4d_impl {
         }                                                                                  \
     }
 
-// After the FP32 coefficients: Wb = bf16(W) (red ends), and per voxel
+// After the FP32 coefficients: Wb = bf16(W) (red ends); per voxel
 // gamma_b = c / D_b, invD_b = 1 / D_b with D_b = D - c * excess, c = gamma*D.
-__global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__restrict__ W,
+// The solve reads b itself (= u at the start of the step) instead of
+// beta = b / D, so beta is overwritten with u.
+__global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__restrict__ u,
+                                                       const float *__restrict__ W,
                                                        const float *__restrict__ gamma,
                                                        const float *__restrict__ diag,
                                                        __nv_bfloat16 *__restrict__ Wb,
                                                        float *__restrict__ gb,
-                                                       float *__restrict__ ib)
+                                                       float *__restrict__ ib,
+                                                       float *__restrict__ beta)
 {
     MX_FOR_TILES(L, s, rp, row, {
         const long long q = (long long)row * L.P + s;
@@ -58,6 +62,7 @@ __global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__
             const float Db = D - c * ex;
             gb[C * L.S + q] = c / Db;
             ib[C * L.S + q] = 1.0f / Db;
+            beta[C * L.S + q] = u[C * L.S + q];
             if (C == 0)
                 for (int f = 0; f < 8; ++f)
                     Wb[(long long)f * L.S + q] = __float2bfloat16_rn(W[(long long)f * L.S + q]);
@@ -65,10 +70,10 @@ __global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__
     })
 }
 
-// Exact residual r = D (beta + gamma sum_f W_f u_nb - u) for every voxel;
-// rho = r / D_b, delta = 0; records (sum r^2, min u, max u) in FP64.
+// Defect pass: r for every voxel; rho = r / D_b, delta = 0; records
+// (sum r^2, min u, max u) in FP64.  b is the prepared beta array.
 __global__ void __launch_bounds__(kPartThreads) k_defect(Layout L, const float *__restrict__ u,
-                                                         const float *__restrict__ beta,
+                                                         const float *__restrict__ b,
                                                          const float *__restrict__ gamma,
                                                          const float *__restrict__ diag,
                                                          const float *__restrict__ W,
@@ -77,54 +82,20 @@ __global__ void __launch_bounds__(kPartThreads) k_defect(Layout L, const float *
                                                          float *__restrict__ delta,
                                                          double *__restrict__ partials)
 {
-    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    Rec3f a = rec3f_init();
     MX_FOR_TILES(L, s, rp, row, {
         const long long q = (long long)row * L.P + s;
         for (int C = 0; C < 2; ++C) {
             if (2 * s + (C ^ rp.p) >= L.n1) continue;
-            const float acc = C ? neighbour_sum<1>(L, u, W, row, s, rp)
-                                : neighbour_sum<0>(L, u + L.S, W, row, s, rp);
-            const float uv = u[C * L.S + q];
-            const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
-            const float r = diag[C * L.S + q] * (ubar - uv);
+            float uv;
+            const float r = C ? flux_residual<1>(L, u, b, gamma, diag, W, row, s, rp, uv)
+                              : flux_residual<0>(L, u, b, gamma, diag, W, row, s, rp, uv);
             rho[C * L.S + q] = r * ib[C * L.S + q];
             delta[C * L.S + q] = 0.0f;
-            const double rd = (double)diag[C * L.S + q] * ((double)ubar - (double)uv);
-            a.sum += rd * rd;
-            a.mn = fmin(a.mn, (double)uv);
-            a.mx = fmax(a.mx, (double)uv);
+            rec3f_add(a, __fmul_rn(r, r), uv);
         }
     })
-    block_write3(a, partials + 3 * blockIdx.x);
-}
-
-// Red-black SOR half sweep on A_b delta = r:
-//   dbar = rho + gamma_b sum_f wb_f delta_nb,  delta <- delta + omega (dbar - delta)
-template <int C>
-__global__ void __launch_bounds__(256, 8) k_sweep_mixed(Layout L, float *__restrict__ d,
-                                                        const float *__restrict__ rho,
-                                                        const float *__restrict__ gb,
-                                                        const __nv_bfloat16 *__restrict__ Wb,
-                                                        float omega)
-{
-    const int chunk = blockIdx.x % L.nchunk;
-    const int jb = blockIdx.x / L.nchunk;
-    const int s = chunk * 32 + threadIdx.x;
-    RowPos rp;
-    rp.j = jb * 8 + threadIdx.y;
-    rp.k = blockIdx.y;
-    rp.l = blockIdx.z;
-    if (rp.j >= L.n2 || s >= L.P) return;
-    rp.p = (rp.j + rp.k + rp.l) & 1;
-    if (2 * s + (C ^ rp.p) >= L.n1) return;
-    const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
-    const long long q = (long long)row * L.P + s;
-    const float *dother = d + (C ? 0 : L.S);
-    float *dself = d + (C ? L.S : 0);
-    const float acc = neighbour_sum<C, false, __nv_bfloat16>(L, dother, Wb, row, s, rp);
-    const float dbar = rho[C * L.S + q] + gb[C * L.S + q] * acc;
-    const float d0 = dself[q];
-    dself[q] = d0 + omega * (dbar - d0);
+    block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
 }
 
 // u <- u + delta over both colour halves (padding holds 0 in both)
@@ -143,30 +114,19 @@ __global__ void __launch_bounds__(256) k_apply(float4 *__restrict__ u,
     }
 }
 
-void launch_mixed_prepare(const Layout &L, const float *W, const float *gamma, const float *diag,
-                          void *Wb, float *gb, float *ib, cudaStream_t st)
+void launch_mixed_prepare(const Layout &L, const float *u, const float *W, const float *gamma,
+                          const float *diag, void *Wb, float *gb, float *ib, float *beta,
+                          cudaStream_t st)
 {
-    k_mixed_prepare<<<kPartBlocks, 256, 0, st>>>(L, W, gamma, diag, (__nv_bfloat16 *)Wb, gb, ib);
+    k_mixed_prepare<<<kPartBlocks, 256, 0, st>>>(L, u, W, gamma, diag, (__nv_bfloat16 *)Wb, gb, ib,
+                                                 beta);
 }
 
-void launch_defect(const Layout &L, const float *u, const float *beta, const float *gamma,
+void launch_defect(const Layout &L, const float *u, const float *b, const float *gamma,
                    const float *diag, const float *W, const float *ib, float *rho, float *delta,
                    double *partials, int nparts, cudaStream_t st)
 {
-    k_defect<<<nparts, kPartThreads, 0, st>>>(L, u, beta, gamma, diag, W, ib, rho, delta,
-                                              partials);
-}
-
-void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *rho,
-                        const float *gb, const void *Wb, float omega, cudaStream_t st)
-{
-    dim3 block(32, 8);
-    dim3 grid((unsigned)(L.nchunk * L.njb), (unsigned)L.n3, (unsigned)L.n4);
-    const __nv_bfloat16 *w = (const __nv_bfloat16 *)Wb;
-    if (colour == 0)
-        k_sweep_mixed<0><<<grid, block, 0, st>>>(L, delta, rho, gb, w, omega);
-    else
-        k_sweep_mixed<1><<<grid, block, 0, st>>>(L, delta, rho, gb, w, omega);
+    k_defect<<<nparts, kPartThreads, 0, st>>>(L, u, b, gamma, diag, W, ib, rho, delta, partials);
 }
 
 void launch_apply(const Layout &L, float *u, const float *delta, cudaStream_t st)

@@ -126,19 +126,23 @@ void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta
                        const float *gamma, const float *W, float omega, unsigned *ctrl, int ctas,
                        int test_wait, cudaStream_t st);
 // mixed precision (mixed_kernels.cu); Wb is a __nv_bfloat16 [8][S] array
-void launch_mixed_prepare(const Layout &L, const float *W, const float *gamma, const float *diag,
-                          void *Wb, float *gb, float *ib, cudaStream_t st);
-void launch_defect(const Layout &L, const float *u, const float *beta, const float *gamma,
+// (launch_mixed_prepare overwrites beta with b = u, which launch_defect reads)
+void launch_mixed_prepare(const Layout &L, const float *u, const float *W, const float *gamma,
+                          const float *diag, void *Wb, float *gb, float *ib, float *beta,
+                          cudaStream_t st);
+void launch_defect(const Layout &L, const float *u, const float *b, const float *gamma,
                    const float *diag, const float *W, const float *ib, float *rho, float *delta,
                    double *partials, int nparts, cudaStream_t st);
+// red-black SOR on the BF16 correction system A_b delta = r (solve_kernels.cu)
 void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *rho,
                         const float *gb, const void *Wb, float omega, cudaStream_t st);
 void launch_apply(const Layout &L, float *u, const float *delta, cudaStream_t st);
 int wave_tiles(const Layout &L);        // tiles per frame of the fused sweep
 int wave_max_ctas_per_sm();             // occupancy limit of the fused sweep
-void launch_residual(const Layout &L, const float *x, const float *beta, const float *gamma,
-                     const float *diag, const float *W, double *partials, int nparts,
-                     cudaStream_t st);
+// residual records of the step or presmoothing system; returns the number of
+// per-block records written to `partials` (at most kResBlocks)
+int launch_residual(const Layout &L, const float *x, const float *beta, const float *gamma,
+                    const float *diag, const float *W, double *partials, cudaStream_t st);
 void launch_reduce_partials(const double *partials, int nparts, double *out, cudaStream_t st);
 
 // message of the last failed handle-free call of this thread (api.cu)
@@ -148,5 +152,9 @@ std::string &handle_free_error();
 // reduction kernels use; the scratch array holds 3 * kPartBlocks doubles.
 constexpr int kPartBlocks = 1024;
 constexpr int kPartThreads = 256;
+// blocks (records) of the residual kernel; the scratch array holds
+// 3 * max(kPartBlocks, kResBlocks) doubles
+constexpr int kResBlocks = 16384;
+constexpr int kPartCap = kResBlocks > kPartBlocks ? kResBlocks : kPartBlocks;
 
 }  // namespace seg4d_impl

@@ -13,7 +13,7 @@
 #include <climits>
 #include <cmath>
 
-#include "seg4d_internal.cuh"
+#include "stencil.cuh"
 
 namespace seg4d_impl {
 
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(kPartThreads) k_smooth_coef(Layout L, const fl
 {
     const float ih2[4] = {inv_h2.x, inv_h2.y, inv_h2.z, inv_h2.w};
     const int nn[4] = {L.n1, L.n2, L.n3, L.n4};
-    double ssum = 0.0, mn = DBL_MAX, mx = -DBL_MAX;
+    Rec3f a = rec3f_init();
     const long long n = 2LL * L.S;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
@@ -471,10 +471,10 @@ __global__ void __launch_bounds__(kPartThreads) k_smooth_coef(Layout L, const fl
         diag[C * L.S + q] = D;
         beta[C * L.S + q] = b / D;
         gamma[C * L.S + q] = sigma_t / D;
-        ssum += (double)b * b;
-        mn = fmin(mn, (double)b);
-        mx = fmax(mx, (double)b);
+        rec3f_add(a, __fmul_rn(b, b), b);
     }
+    const Acc3 ad = rec3f_acc(a);
+    double ssum = ad.sum, mn = ad.mn, mx = ad.mx;
     // block reduction of (sum, min, max)
     for (int o = 16; o > 0; o >>= 1) {
         ssum += __shfl_down_sync(0xffffffffu, ssum, o);

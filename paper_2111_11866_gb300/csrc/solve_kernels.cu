@@ -39,43 +39,56 @@ namespace seg4d_impl {
 //   ubar = (b + c sum_f w_f u_nb) / D   (the Gauss-Seidel value of Eq. gsee,
 //   here = beta + gamma * sum_f w_f u_nb with beta = b/D, gamma = c/D), then
 //   u <- u + omega (ubar - u)           (Eq. 5.33).
-// Grid: x = 32-slot chunk + nchunk * (8-row block along y), y = k, z = l;
-// block (32, 8).  A warp covers 32 consecutive slots of one row.
-template <int C>
-__global__ void __launch_bounds__(256, 8) k_sweep(Layout L, float *__restrict__ x,
-                                               const float *__restrict__ beta,
-                                               const float *__restrict__ gamma,
-                                               const float *__restrict__ W, float omega)
+// N voxels per thread (relax_vec): a warp covers 32 N consecutive slots of
+// one row, a block (32, 8) 8 rows; grid (row chunks x y-blocks, n3, n4).  The
+// black pass walks the grid backwards, so it starts on the data the red pass
+// touched last, which is still in L2.  The same kernel with BF16 weights
+// sweeps the correction system of the mixed-precision solve.
+template <int C, typename WT, int N>
+__global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_sweep_vec(
+    Layout L, float *__restrict__ x, const float *__restrict__ B, const float *__restrict__ Gm,
+    const WT *__restrict__ W, float omega)
 {
-    const int chunk = blockIdx.x % L.nchunk;
-    const int jb = blockIdx.x / L.nchunk;
-    const int s = chunk * 32 + threadIdx.x;
+    const int nch = (L.P + 32 * N - 1) / (32 * N);
+    const int bx = C ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    const int chunk = bx % nch;
+    const int jb = bx / nch;
     RowPos rp;
     rp.j = jb * 8 + threadIdx.y;
-    rp.k = blockIdx.y;
-    rp.l = blockIdx.z;
-    if (rp.j >= L.n2 || s >= L.P) return;
+    rp.k = C ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+    rp.l = C ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    if (rp.j >= L.n2) return;   // the whole warp
     rp.p = (rp.j + rp.k + rp.l) & 1;
-    if (2 * s + (C ^ rp.p) >= L.n1) return;
+    const int s0 = chunk * 32 * N + N * threadIdx.x;
+    const bool act = s0 < L.P && 2 * s0 + (C ^ rp.p) < L.n1;
     const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
-    const long long q = (long long)row * L.P + s;
-    const float *xo = x + (C ? 0 : L.S);
-    float *xs = x + (C ? L.S : 0);
-    const float acc = neighbour_sum<C>(L, xo, W, row, s, rp);
-    const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
-    const float u0 = xs[q];
-    xs[q] = u0 + omega * (ubar - u0);
+    relax_vec<C, WT, N>(L, x, B, Gm, W, omega, act, row, s0, rp);
+}
+
+template <typename WT, int N>
+void launch_vec(const Layout &L, int colour, float *x, const float *B, const float *Gm,
+                const WT *W, float omega, cudaStream_t st)
+{
+    dim3 block(32, 8);
+    dim3 grid((unsigned)(((L.P + 32 * N - 1) / (32 * N)) * L.njb), (unsigned)L.n3,
+              (unsigned)L.n4);
+    if (colour == 0)
+        k_sweep_vec<0, WT, N><<<grid, block, 0, st>>>(L, x, B, Gm, W, omega);
+    else
+        k_sweep_vec<1, WT, N><<<grid, block, 0, st>>>(L, x, B, Gm, W, omega);
 }
 
 void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,
                   const float *W, float omega, cudaStream_t st)
 {
-    dim3 block(32, 8);
-    dim3 grid((unsigned)(L.nchunk * L.njb), (unsigned)L.n3, (unsigned)L.n4);
-    if (colour == 0)
-        k_sweep<0><<<grid, block, 0, st>>>(L, x, beta, gamma, W, omega);
-    else
-        k_sweep<1><<<grid, block, 0, st>>>(L, x, beta, gamma, W, omega);
+    launch_vec<float, kVecF32>(L, colour, x, beta, gamma, W, omega, st);
+}
+
+void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *rho,
+                        const float *gb, const void *Wb, float omega, cudaStream_t st)
+{
+    launch_vec<__nv_bfloat16, kVecBF16>(L, colour, delta, rho, gb, (const __nv_bfloat16 *)Wb,
+                                        omega, st);
 }
 
 // ------------------------------------------ fused red-black wavefront sweep
@@ -188,9 +201,8 @@ __device__ __forceinline__ void wave_rows(const Layout &L, float *__restrict__ x
                 if (rp.j < L.n2 && s < L.P && 2 * s + (C ^ rp.p) < L.n1) {
                     const long long q = rb + s;
                     const float acc = neighbour_sum<C, true>(L, xo, W, row, s, rp);
-                    const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
-                    const float u0 = __ldcg(xs + q);
-                    val[r][m] = u0 + omega * (ubar - u0);
+                    val[r][m] = relax(__ldcg(xs + q), beta[C * L.S + q], gamma[C * L.S + q],
+                                      acc, omega);
                 }
             }
         }
@@ -287,39 +299,68 @@ void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta
 
 // --------------------------------------------------------------- residual
 
-// r_v = b_v - (A u)_v = D_v (ubar_v - u_v) for every voxel; per-block records
-// of (sum r^2, min u, max u) in FP64.
-__global__ void __launch_bounds__(kPartThreads) k_residual(Layout L, const float *__restrict__ x,
-                                                           const float *__restrict__ beta,
-                                                           const float *__restrict__ gamma,
-                                                           const float *__restrict__ diag,
-                                                           const float *__restrict__ W,
-                                                           double *__restrict__ partials)
+// r_v = b_v - (A u)_v = D_v (ubar_v - u_v) for every voxel, with ubar the
+// sweep's Gauss-Seidel value; records (sum r^2, min u, max u) per block.
+// Work item t = 2 * tile + colour, tile = one block of the sweep grid
+// (32 N slots x 8 rows at one (k, l)); blocks stride over the items.
+template <int N>
+__global__ void __launch_bounds__(256, 3) k_residual_vec(
+    Layout L, const float *__restrict__ x, const float *__restrict__ beta,
+    const float *__restrict__ gamma, const float *__restrict__ diag, const float *__restrict__ W,
+    double *__restrict__ partials)
 {
-    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
-    FOR_TILES(L, s, rp, row, {
-        const long long q = (long long)row * L.P + s;
-        for (int C = 0; C < 2; ++C) {
-            if (2 * s + (C ^ rp.p) < L.n1) {
-                const float acc = C ? neighbour_sum<1>(L, x, W, row, s, rp)
-                                    : neighbour_sum<0>(L, x + L.S, W, row, s, rp);
-                const float u = x[C * L.S + q];
-                const float ubar = beta[C * L.S + q] + gamma[C * L.S + q] * acc;
-                const double r = (double)diag[C * L.S + q] * ((double)ubar - (double)u);
-                a.sum += r * r;
-                a.mn = fmin(a.mn, (double)u);
-                a.mx = fmax(a.mx, (double)u);
-            }
+    const int nch = (L.P + 32 * N - 1) / (32 * N);
+    const long long items = 2LL * nch * L.njb * L.n3 * L.n4;
+    Rec3f a = rec3f_init();
+    for (long long t = blockIdx.x; t < items; t += gridDim.x) {
+        const int C = (int)(t & 1);
+        long long r = t >> 1;
+        const int chunk = (int)(r % nch);
+        r /= nch;
+        const int jb = (int)(r % L.njb);
+        r /= L.njb;
+        RowPos rp;
+        rp.k = (int)(r % L.n3);
+        rp.l = (int)(r / L.n3);
+        rp.j = jb * 8 + (int)(threadIdx.x >> 5);
+        rp.p = (rp.j + rp.k + rp.l) & 1;
+        const int s0 = chunk * 32 * N + N * (int)(threadIdx.x & 31);
+        // whole warps leave together (rows past n2); lanes past the row end stay
+        // for the shuffles of gather_vec
+        if (rp.j >= L.n2) continue;
+        const bool act = s0 < L.P && 2 * s0 + (C ^ rp.p) < L.n1;
+        const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
+        const long long q = (long long)row * L.P + s0 + (C ? L.S : 0);
+        float Xs[N], Bp[N], Gp[N], Dp[N], acc[N];
+        ldv<N>(Xs, act, x + q);
+        ldv<N>(Bp, act, beta + q);
+        ldv<N>(Gp, act, gamma + q);
+        ldv<N>(Dp, act, diag + q);
+        if (C)
+            gather_vec<1, float, N>(L, x, W, act, row, s0, rp, acc);
+        else
+            gather_vec<0, float, N>(L, x, W, act, row, s0, rp, acc);
+        if (!act) continue;
+        const int e = C ^ rp.p;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            if (2 * (s0 + m) + e >= L.n1) continue;
+            const float ubar = __fmaf_rn(Gp[m], acc[m], Bp[m]);
+            const float res = __fmul_rn(Dp[m], __fsub_rn(ubar, Xs[m]));
+            rec3f_add(a, __fmul_rn(res, res), Xs[m]);
         }
-    })
-    block_write3(a, partials + 3 * blockIdx.x);
+    }
+    block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
 }
 
-void launch_residual(const Layout &L, const float *x, const float *beta, const float *gamma,
-                     const float *diag, const float *W, double *partials, int nparts,
-                     cudaStream_t st)
+int launch_residual(const Layout &L, const float *x, const float *beta, const float *gamma,
+                    const float *diag, const float *W, double *partials, cudaStream_t st)
 {
-    k_residual<<<nparts, kPartThreads, 0, st>>>(L, x, beta, gamma, diag, W, partials);
+    const int N = kVecF32;
+    const long long items = 2LL * ((L.P + 32 * N - 1) / (32 * N)) * L.njb * L.n3 * L.n4;
+    const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
+    k_residual_vec<kVecF32><<<blocks, 256, 0, st>>>(L, x, beta, gamma, diag, W, partials);
+    return blocks;
 }
 
 // Deterministic final reduction of the per-block records (one block).
@@ -327,6 +368,7 @@ __global__ void __launch_bounds__(1024) k_reduce(const double *__restrict__ part
                                                  double *__restrict__ out)
 {
     Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+#pragma unroll 4
     for (int b = threadIdx.x; b < n; b += blockDim.x)
         a = acc3_merge(a, Acc3{partials[3 * b], partials[3 * b + 1], partials[3 * b + 2]});
     block_write3(a, out);
@@ -350,22 +392,22 @@ __global__ void __launch_bounds__(kPartThreads) k_step_coef(Layout L, const floa
                                                             float *__restrict__ W,
                                                             double *__restrict__ partials)
 {
-    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    Rec3f a = rec3f_init();
     FOR_TILES(L, s, rp, row, {
         const long long q = (long long)row * L.P + s;
-#pragma unroll 1
+        _Pragma("unroll 1")
         for (int C = 0; C < 2; ++C) {
             const int i = 2 * s + (C ^ rp.p);
             if (i < L.n1) {
                 float g2[8];
                 face_grad_sq8(L, u, i, rp.j, rp.k, rp.l, K.inv_h, g2);
                 float sum = 0.0f;
-#pragma unroll
+                _Pragma("unroll")
                 for (int f = 0; f < 8; ++f) sum += g2[f];
                 const float Abar = sqrtf(K.eps2 + 0.125f * sum);
                 const float cc = K.tau * Abar;
                 float wsum = 0.0f;
-#pragma unroll
+                _Pragma("unroll")
                 for (int f = 0; f < 8; ++f) {
                     const float Af = sqrtf(K.eps2 + g2[f]);
                     const float w = G[((long long)C * 8 + f) * L.S + q] / Af * K.inv_h2[f >> 1];
@@ -377,13 +419,11 @@ __global__ void __launch_bounds__(kPartThreads) k_step_coef(Layout L, const floa
                 diag[C * L.S + q] = D;
                 beta[C * L.S + q] = b / D;
                 gamma[C * L.S + q] = cc / D;
-                a.sum += (double)b * (double)b;
-                a.mn = fmin(a.mn, (double)b);
-                a.mx = fmax(a.mx, (double)b);
+                rec3f_add(a, __fmul_rn(b, b), b);
             }
         }
     })
-    block_write3(a, partials + 3 * blockIdx.x);
+    block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
 }
 
 void launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,

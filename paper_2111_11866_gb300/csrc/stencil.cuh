@@ -78,6 +78,23 @@ __device__ __forceinline__ float ldu(const float *p)
 __device__ __forceinline__ float ldw(const float *p) { return *p; }
 __device__ __forceinline__ float ldw(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 
+// Relaxation arithmetic with every rounding explicit (no contraction left to
+// the compiler), so that all sweep kernels -- one voxel or two per thread,
+// fused or not -- produce the same bits:
+//   acc = sum over faces of w_f x_f (products rounded, fixed addition tree),
+//   x  <- x + omega (B + G acc - x).
+__device__ __forceinline__ float sum8(float t0, float t1, float t2, float t3, float t4, float t5,
+                                      float t6, float t7)
+{
+    return __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), __fadd_rn(t2, t3)),
+                     __fadd_rn(__fadd_rn(t4, t5), __fadd_rn(t6, t7)));
+}
+
+__device__ __forceinline__ float relax(float x, float B, float G, float acc, float omega)
+{
+    return __fmaf_rn(omega, __fsub_rn(__fmaf_rn(G, acc, B), x), x);
+}
+
 template <int C, bool kCG = false, typename WT = float>
 __device__ __forceinline__ float neighbour_sum(const Layout &L, const float *__restrict__ xo,
                                                const WT *__restrict__ W, int row, int s,
@@ -92,28 +109,234 @@ __device__ __forceinline__ float neighbour_sum(const Layout &L, const float *__r
     float t0, t1, t2, t3, t4, t5, t6, t7;
     if (C == 0) {
         const int sxm = s - 1 + rp.p, sxp = s + rp.p;
-        t0 = sxm >= 0 ? ldw(W + 0 * S + q) * ldu<kCG>(xo + rb + sxm) : 0.0f;
-        t1 = sxp < L.P ? ldw(W + 1 * S + q) * ldu<kCG>(xo + rb + sxp) : 0.0f;
-        t2 = rp.j > 0 ? ldw(W + 2 * S + q) * ldu<kCG>(xo + q - dy) : 0.0f;
-        t3 = rp.j + 1 < L.n2 ? ldw(W + 3 * S + q) * ldu<kCG>(xo + q + dy) : 0.0f;
-        t4 = rp.k > 0 ? ldw(W + 4 * S + q) * ldu<kCG>(xo + q - dz) : 0.0f;
-        t5 = rp.k + 1 < L.n3 ? ldw(W + 5 * S + q) * ldu<kCG>(xo + q + dz) : 0.0f;
-        t6 = rp.l > 0 ? ldw(W + 6 * S + q) * ldu<kCG>(xo + q - dt) : 0.0f;
-        t7 = rp.l + 1 < L.n4 ? ldw(W + 7 * S + q) * ldu<kCG>(xo + q + dt) : 0.0f;
+        t0 = sxm >= 0 ? __fmul_rn(ldw(W + 0 * S + q), ldu<kCG>(xo + rb + sxm)) : 0.0f;
+        t1 = sxp < L.P ? __fmul_rn(ldw(W + 1 * S + q), ldu<kCG>(xo + rb + sxp)) : 0.0f;
+        t2 = rp.j > 0 ? __fmul_rn(ldw(W + 2 * S + q), ldu<kCG>(xo + q - dy)) : 0.0f;
+        t3 = rp.j + 1 < L.n2 ? __fmul_rn(ldw(W + 3 * S + q), ldu<kCG>(xo + q + dy)) : 0.0f;
+        t4 = rp.k > 0 ? __fmul_rn(ldw(W + 4 * S + q), ldu<kCG>(xo + q - dz)) : 0.0f;
+        t5 = rp.k + 1 < L.n3 ? __fmul_rn(ldw(W + 5 * S + q), ldu<kCG>(xo + q + dz)) : 0.0f;
+        t6 = rp.l > 0 ? __fmul_rn(ldw(W + 6 * S + q), ldu<kCG>(xo + q - dt)) : 0.0f;
+        t7 = rp.l + 1 < L.n4 ? __fmul_rn(ldw(W + 7 * S + q), ldu<kCG>(xo + q + dt)) : 0.0f;
     } else {
         const int sxm = s - rp.p, sxp = s + 1 - rp.p;
-        t0 = sxm >= 0 ? ldw(W + 1 * S + rb + sxm) * ldu<kCG>(xo + rb + sxm) : 0.0f;
-        t1 = sxp < L.P ? ldw(W + 0 * S + rb + sxp) * ldu<kCG>(xo + rb + sxp) : 0.0f;
-        t2 = rp.j > 0 ? ldw(W + 3 * S + q - dy) * ldu<kCG>(xo + q - dy) : 0.0f;
-        t3 = rp.j + 1 < L.n2 ? ldw(W + 2 * S + q + dy) * ldu<kCG>(xo + q + dy) : 0.0f;
-        t4 = rp.k > 0 ? ldw(W + 5 * S + q - dz) * ldu<kCG>(xo + q - dz) : 0.0f;
-        t5 = rp.k + 1 < L.n3 ? ldw(W + 4 * S + q + dz) * ldu<kCG>(xo + q + dz) : 0.0f;
-        t6 = rp.l > 0 ? ldw(W + 7 * S + q - dt) * ldu<kCG>(xo + q - dt) : 0.0f;
-        t7 = rp.l + 1 < L.n4 ? ldw(W + 6 * S + q + dt) * ldu<kCG>(xo + q + dt) : 0.0f;
+        t0 = sxm >= 0 ? __fmul_rn(ldw(W + 1 * S + rb + sxm), ldu<kCG>(xo + rb + sxm)) : 0.0f;
+        t1 = sxp < L.P ? __fmul_rn(ldw(W + 0 * S + rb + sxp), ldu<kCG>(xo + rb + sxp)) : 0.0f;
+        t2 = rp.j > 0 ? __fmul_rn(ldw(W + 3 * S + q - dy), ldu<kCG>(xo + q - dy)) : 0.0f;
+        t3 = rp.j + 1 < L.n2 ? __fmul_rn(ldw(W + 2 * S + q + dy), ldu<kCG>(xo + q + dy)) : 0.0f;
+        t4 = rp.k > 0 ? __fmul_rn(ldw(W + 5 * S + q - dz), ldu<kCG>(xo + q - dz)) : 0.0f;
+        t5 = rp.k + 1 < L.n3 ? __fmul_rn(ldw(W + 4 * S + q + dz), ldu<kCG>(xo + q + dz)) : 0.0f;
+        t6 = rp.l > 0 ? __fmul_rn(ldw(W + 7 * S + q - dt), ldu<kCG>(xo + q - dt)) : 0.0f;
+        t7 = rp.l + 1 < L.n4 ? __fmul_rn(ldw(W + 6 * S + q + dt), ldu<kCG>(xo + q + dt)) : 0.0f;
     }
-    return ((t0 + t1) + (t2 + t3)) + ((t4 + t5) + (t6 + t7));
+    return sum8(t0, t1, t2, t3, t4, t5, t6, t7);
 }
 
+// ------------------------------------------------ N voxels per thread
+
+// Voxels per thread of the sweep kernels (2: float2 loads of x and the
+// coefficients, 8- or 4-byte loads of the weights; 4 costs occupancy), and
+// the resident 256-thread blocks per SM they are compiled for.
+#ifndef SEG4D_VEC_F32
+#define SEG4D_VEC_F32 2
+#endif
+#ifndef SEG4D_VEC_BF16
+#define SEG4D_VEC_BF16 2
+#endif
+constexpr int kVecF32 = SEG4D_VEC_F32;
+constexpr int kVecBF16 = SEG4D_VEC_BF16;
+static_assert((kVecF32 == 2 || kVecF32 == 4) && (kVecBF16 == 2 || kVecBF16 == 4),
+              "2 or 4 voxels per thread (P is a multiple of 4)");
+#ifndef SEG4D_VEC2_MINB
+#define SEG4D_VEC2_MINB 4
+#endif
+#ifndef SEG4D_VEC4_MINB
+#define SEG4D_VEC4_MINB 2
+#endif
+template <int N>
+constexpr int vec_min_blocks() { return N == 2 ? SEG4D_VEC2_MINB : SEG4D_VEC4_MINB; }
+
+// N-wide vector loads (N = 2 or 4 consecutive slots, N-aligned) into float
+// arrays; a load whose condition is false yields zeros.
+template <int N>
+__device__ __forceinline__ void ldv(float (&v)[N], bool c, const float *p)
+{
+    if constexpr (N == 2) {
+        const float2 t = c ? *reinterpret_cast<const float2 *>(p) : make_float2(0.0f, 0.0f);
+        v[0] = t.x;
+        v[1] = t.y;
+    } else {
+        const float4 t =
+            c ? *reinterpret_cast<const float4 *>(p) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void ldv(float (&v)[N], bool c, const __nv_bfloat16 *p)
+{
+    if constexpr (N == 2) {
+        const unsigned t = c ? *reinterpret_cast<const unsigned *>(p) : 0u;
+        v[0] = __uint_as_float(t << 16);
+        v[1] = __uint_as_float(t & 0xFFFF0000u);
+    } else {
+        const uint2 t = c ? *reinterpret_cast<const uint2 *>(p) : make_uint2(0u, 0u);
+        v[0] = __uint_as_float(t.x << 16);
+        v[1] = __uint_as_float(t.x & 0xFFFF0000u);
+        v[2] = __uint_as_float(t.y << 16);
+        v[3] = __uint_as_float(t.y & 0xFFFF0000u);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void stv(float *p, const float (&v)[N])
+{
+    if constexpr (N == 2)
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    else
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// Neighbour sums of the N voxels in slots s0 .. s0+N-1 (s0 a multiple of N)
+// of colour C in row `row`: acc[m] = sum_f w_f x_nb(f) with the arithmetic
+// of neighbour_sum (products rounded, fixed addition tree, a face outside
+// the grid contributes exactly 0).  x is the [2][S] iterate, W the [8][S]
+// face weights by red end (FP32, or BF16 widened exactly).  Every load is an
+// N-wide vector load, all issued before any is used; a caller that needs
+// more per-voxel data issues those loads before calling, so that they are in
+// flight together.  The x-neighbour just past either end of the group (and,
+// for black voxels, its face weight) comes from the adjacent lane by shuffle
+// when that lane holds the adjacent group of the same row, and is loaded
+// otherwise.  All 32 lanes of the warp must call this; lanes without a group
+// pass act = false (their acc is not set).
+template <int C, typename WT, int N>
+__device__ __forceinline__ void gather_vec(const Layout &L, const float *__restrict__ x,
+                                           const WT *__restrict__ W, bool act, int row, int s0,
+                                           const RowPos &rp, float (&acc)[N])
+{
+    const long long S = L.S;
+    const long long q = (long long)row * L.P + s0;
+    const float *xo = x + (C ? 0 : S);
+    const int e = C ^ rp.p;   // i = 2 s + e
+    const long long dy = L.P, dz = (long long)L.n2 * L.P, dt = (long long)L.n2 * L.n3 * L.P;
+    // y, z, t faces f = 2..7: neighbour offset and presence
+    const long long off[6] = {-dy, dy, -dz, dz, -dt, dt};
+    const bool in[6] = {act && rp.j > 0, act && rp.j + 1 < L.n2, act && rp.k > 0,
+                        act && rp.k + 1 < L.n3, act && rp.l > 0, act && rp.l + 1 < L.n4};
+    float X[N], W0[N], W1[N], a[6][N], y[6][N];
+    ldv<N>(X, act, xo + q);
+    // x-direction weights: red owns faces 0 (-x) and 1 (+x); black reads
+    // face 1 of the red voxel on its left and face 0 of the one on its right
+    ldv<N>(W0, act, W + 0 * S + q);
+    ldv<N>(W1, act, W + 1 * S + q);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        // red: own face f+2; black: the opposite face of the red neighbour
+        const long long wi = C == 0 ? (long long)(f + 2) * S + q
+                                    : (long long)((f + 2) ^ 1) * S + q + off[f];
+        ldv<N>(a[f], in[f], W + wi);
+        ldv<N>(y[f], in[f], xo + q + off[f]);
+    }
+    const unsigned key = act ? (unsigned)q : 0xFFFFFFFFu;   // q is even; the sentinel odd
+    const unsigned keyL = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+    const unsigned keyR = __shfl_down_sync(0xFFFFFFFFu, key, 1);
+    const float xLs = __shfl_up_sync(0xFFFFFFFFu, X[N - 1], 1);
+    const float xRs = __shfl_down_sync(0xFFFFFFFFu, X[0], 1);
+    const float wLs = __shfl_up_sync(0xFFFFFFFFu, W1[N - 1], 1);
+    const float wRs = __shfl_down_sync(0xFFFFFFFFu, W0[0], 1);
+    if (!act) return;
+    const bool hasL = s0 > 0, hasR = s0 + N < L.P;
+    const bool shL = hasL && keyL == (unsigned)(q - N);
+    const bool shR = hasR && keyR == (unsigned)(q + N);
+    float xl = 0.0f, xr = 0.0f, wl = 0.0f, wr = 0.0f;
+    if (e == 0) {
+        xl = shL ? xLs : (hasL ? xo[q - 1] : 0.0f);
+        if (C == 1) wl = shL ? wLs : (hasL ? ldw(W + 1 * S + q - 1) : 0.0f);
+    } else {
+        xr = shR ? xRs : (hasR ? xo[q + N] : 0.0f);
+        if (C == 1) wr = shR ? wRs : (hasR ? ldw(W + 0 * S + q + N) : 0.0f);
+    }
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        // e = 0: x-neighbours of slot s are slots s-1 and s; e = 1: s and s+1
+        const float xm = e == 0 ? (m == 0 ? xl : X[m - 1]) : X[m];
+        const float xp = e == 0 ? X[m] : (m == N - 1 ? xr : X[m + 1]);
+        float wm, wp;
+        if (C == 0) {
+            wm = W0[m];
+            wp = W1[m];
+        } else {
+            wm = e == 0 ? (m == 0 ? wl : W1[m - 1]) : W1[m];
+            wp = e == 0 ? W0[m] : (m == N - 1 ? wr : W0[m + 1]);
+        }
+        const bool inm = e == 1 || m > 0 || hasL;
+        const bool inp = e == 0 || m < N - 1 || hasR;
+        acc[m] = sum8(inm ? __fmul_rn(wm, xm) : 0.0f, inp ? __fmul_rn(wp, xp) : 0.0f,
+                      in[0] ? __fmul_rn(a[0][m], y[0][m]) : 0.0f,
+                      in[1] ? __fmul_rn(a[1][m], y[1][m]) : 0.0f,
+                      in[2] ? __fmul_rn(a[2][m], y[2][m]) : 0.0f,
+                      in[3] ? __fmul_rn(a[3][m], y[3][m]) : 0.0f,
+                      in[4] ? __fmul_rn(a[4][m], y[4][m]) : 0.0f,
+                      in[5] ? __fmul_rn(a[5][m], y[5][m]) : 0.0f);
+    }
+}
+
+// One colour-C relaxation of the N voxels of a group (see gather_vec):
+// x <- x + omega (B + G acc - x) with B and G the [2][S] per-voxel
+// coefficients, the arithmetic of neighbour_sum + relax.  Slots past the row
+// end (i >= n1) are padding and keep their value (zero).
+template <int C, typename WT, int N>
+__device__ __forceinline__ void relax_vec(const Layout &L, float *__restrict__ x,
+                                          const float *__restrict__ B,
+                                          const float *__restrict__ Gm,
+                                          const WT *__restrict__ W, float omega, bool act,
+                                          int row, int s0, const RowPos &rp)
+{
+    const long long S = L.S;
+    const long long q = (long long)row * L.P + s0;
+    float *xs = x + (C ? S : 0);
+    float Xs[N], Bp[N], Gp[N], acc[N];
+    ldv<N>(Xs, act, xs + q);
+    ldv<N>(Bp, act, B + C * S + q);
+    ldv<N>(Gp, act, Gm + C * S + q);
+    gather_vec<C, WT, N>(L, x, W, act, row, s0, rp, acc);
+    if (!act) return;
+    const int e = C ^ rp.p;
+    float out[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m)
+        out[m] = 2 * (s0 + m) + e < L.n1 ? relax(Xs[m], Bp[m], Gp[m], acc[m], omega) : Xs[m];
+    stv<N>(xs + q, out);
+}
+
+// Per-thread record (sum of squares, min, max) in FP32, the sum compensated
+// (TwoSum, error term carried separately), so that a thread's share is
+// accurate to FP32 rounding of its final value; converted to the FP64 Acc3
+// for the block and grid reductions.  Keeps FP64 arithmetic (a slow pipe on
+// this part) out of the per-voxel loop.
+struct Rec3f {
+    float s, c, mn, mx;
+};
+
+__device__ __forceinline__ Rec3f rec3f_init() { return {0.0f, 0.0f, FLT_MAX, -FLT_MAX}; }
+
+__device__ __forceinline__ void rec3f_add(Rec3f &a, float v2, float u)
+{
+    const float t = __fadd_rn(a.s, v2);
+    const float bp = __fsub_rn(t, a.s);
+    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(v2, bp));
+    a.s = t;
+    a.c = __fadd_rn(a.c, err);
+    a.mn = fminf(a.mn, u);
+    a.mx = fmaxf(a.mx, u);
+}
+
+__device__ __forceinline__ Acc3 rec3f_acc(const Rec3f &a)
+{
+    return {(double)a.s + (double)a.c, (double)a.mn, (double)a.mx};
+}
 
 // ------------------------------------------------------- step coefficients
 
@@ -179,6 +402,109 @@ __device__ inline void face_grad_sq8(const Layout &L, const float *__restrict__ 
     }
 }
 
+// Flux form of the off-diagonal part: sum over the interior faces of
+// w_f (x_self - x_nb(f)); the differences are formed before weighting, so
+// the sum is accurate to its own size rather than to the size of x.
+// Also returns the interior weight sum.
+template <int C>
+__device__ __forceinline__ float neighbour_flux(const Layout &L, const float *__restrict__ xo,
+                                                const float *__restrict__ W, int row, int s,
+                                                const RowPos &rp, float xs, float &wint)
+{
+    const long long S = L.S;
+    const long long rb = (long long)row * L.P;
+    const long long q = rb + s;
+    const long long dy = L.P, dz = (long long)L.n2 * L.P, dt = (long long)L.n2 * L.n3 * L.P;
+    long long wi[8], xi[8];
+    bool in[8];
+    const int i = 2 * s + (C ^ rp.p);
+    in[0] = i >= 1;
+    in[1] = i + 1 < L.n1;
+    in[2] = rp.j > 0;
+    in[3] = rp.j + 1 < L.n2;
+    in[4] = rp.k > 0;
+    in[5] = rp.k + 1 < L.n3;
+    in[6] = rp.l > 0;
+    in[7] = rp.l + 1 < L.n4;
+    if (C == 0) {
+        xi[0] = rb + s - 1 + rp.p;
+        xi[1] = rb + s + rp.p;
+        for (int f = 0; f < 8; ++f) wi[f] = (long long)f * S + q;
+    } else {
+        xi[0] = rb + s - rp.p;
+        xi[1] = rb + s + 1 - rp.p;
+        wi[0] = 1 * S + xi[0];
+        wi[1] = 0 * S + xi[1];
+        wi[2] = 3 * S + q - dy;
+        wi[3] = 2 * S + q + dy;
+        wi[4] = 5 * S + q - dz;
+        wi[5] = 4 * S + q + dz;
+        wi[6] = 7 * S + q - dt;
+        wi[7] = 6 * S + q + dt;
+    }
+    xi[2] = q - dy;
+    xi[3] = q + dy;
+    xi[4] = q - dz;
+    xi[5] = q + dz;
+    xi[6] = q - dt;
+    xi[7] = q + dt;
+    float acc = 0.0f, ws = 0.0f;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+        if (!in[f]) continue;
+        const float w = W[wi[f]];
+        acc += w * (xs - xo[xi[f]]);
+        ws += w;
+    }
+    wint = ws;
+    return acc;
+}
+
+// Sum of the weights of a voxel's faces to the Dirichlet ring (0 away from
+// the boundary).  A red voxel stores all 8 of its weights; a black voxel's
+// boundary weights are stored nowhere, so their sum is (D - 1)/c minus the
+// interior sum wint.
+template <int C>
+__device__ __forceinline__ float boundary_weight(const Layout &L, const float *__restrict__ W,
+                                                 long long q, int i, const RowPos &rp, float D,
+                                                 float c, float wint)
+{
+    const bool in[8] = {i >= 1, i + 1 < L.n1, rp.j > 0, rp.j + 1 < L.n2,
+                        rp.k > 0, rp.k + 1 < L.n3, rp.l > 0, rp.l + 1 < L.n4};
+    bool bnd = false;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) bnd |= !in[f];
+    if (!bnd) return 0.0f;
+    if (C == 1) return (D - 1.0f) / c - wint;
+    float sb = 0.0f;
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+        if (!in[f]) sb += W[(long long)f * L.S + q];
+    return sb;
+}
+
+// Exact residual of one voxel in flux form,
+//   r = (b - u) - c (sum_f w_f (u - u_nb) + u * boundary weights),
+// the same A u as D u - c sum_f w_f u_nb, but the differences u - u_nb are
+// small and exact, so r carries far less rounding noise than D (ubar - u) and
+// the correction sweeps do not chase it.
+template <int C>
+__device__ __forceinline__ float flux_residual(const Layout &L, const float *__restrict__ u,
+                                               const float *__restrict__ b,
+                                               const float *__restrict__ gamma,
+                                               const float *__restrict__ diag,
+                                               const float *__restrict__ W, int row, int s,
+                                               const RowPos &rp, float &uv)
+{
+    const long long q = (long long)row * L.P + s;
+    uv = u[C * L.S + q];
+    float wint;
+    const float flux = neighbour_flux<C>(L, u + (C ? 0 : L.S), W, row, s, rp, uv, wint);
+    const float D = diag[C * L.S + q];
+    const float c = gamma[C * L.S + q] * D;
+    const float wb = boundary_weight<C>(L, W, q, 2 * s + (C ^ rp.p), rp, D, c, wint);
+    return (b[C * L.S + q] - uv) - c * (flux + uv * wb);
+}
 
 // Sum over the interior faces of (w_f - bf16(w_f)) for the voxel in slot s
 // (red voxels own their weights, black voxels read them across the face).

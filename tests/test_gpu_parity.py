@@ -254,11 +254,16 @@ def test_device_pointers_roundtrip():
 
 # ---------------------------------------------------------------- fused sweep
 
-@pytest.mark.parametrize("dims", [(69, 21, 13, 5), (40, 17, 6, 1), (31, 9, 5, 2), (64, 24, 12, 7),
-                                  (3, 2, 1, 4)])
-def test_fused_sweep_bit_identical_to_two_launch_sweep(dims):
-    """The wavefront sweep performs exactly the red-then-black sweeps: same
-    iterates bit for bit, same sweep counts (ragged tiles, n4 = 1 and 2)."""
+SWEEP_DIMS = [(69, 21, 13, 5), (40, 17, 6, 1), (31, 9, 5, 2), (64, 24, 12, 7), (3, 2, 1, 4),
+              (201, 7, 5, 3), (130, 9, 4, 2)]
+
+
+@pytest.mark.parametrize("dims", SWEEP_DIMS)
+def test_sweep_variants_bit_identical(dims):
+    """The wavefront sweep (0, one voxel per thread) performs exactly the
+    red-then-black sweeps of the per-colour launches (1, two voxels per
+    thread): same iterates bit for bit, same sweep counts (ragged rows and
+    tiles, rows longer than one warp's 64 slots, n4 = 1 and 2)."""
     n1, n2, n3, n4 = dims
     image = synth.random_field(sum(dims), dims)
     seeds = [(n1 // 2, n2 // 2, n3 // 2, 0), (n1 // 3, n2 // 3, n3 // 3, n4 - 1)]
