@@ -207,17 +207,17 @@ struct SolveOut {
 };
 
 // Red-black SOR on x with the coefficients currently in beta/gamma/diag/W;
-// the per-block records of ||b||^2 must be in `partials` (written by the
-// coefficient kernel).  Stopping rule: ||b - A x||_2 <= tol ||b||_2, tested
+// the brec per-block records of ||b||^2 must be in `partials` (written by
+// the coefficient kernel).  Stopping rule: ||b - A x||_2 <= tol ||b||_2, tested
 // before the first sweep and after every check_every sweeps.
 // With `mixed` (precision 1) every check is a defect pass (exact residual,
 // right-hand side of the BF16 correction system, delta = 0), the sweeps run
 // on A_b delta = r with BF16 weights and u += delta follows each batch.
-seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_iters,
+seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol, int max_iters,
                           int check_every, SolveOut &out, bool mixed = false)
 {
     const Layout &L = h->L;
-    seg4d_status st = reduce_into(h, 0);   // scal[0..2] = sum b^2, min b, max b
+    seg4d_status st = reduce_into(h, 0, brec);   // scal[0..2] = sum b^2, min b, max b
     if (st) return st;
     int it = 0;
     bool timed_batch = false;
@@ -239,8 +239,8 @@ seg4d_status solve_system(seg4d *h, float *x, double omega, double tol, int max_
     for (;;) {
         int nrec = kPartBlocks;
         if (mixed)
-            launch_defect(L, x, h->beta, h->gamma, h->diag, h->W, h->ib, h->rho, h->dlt,
-                          h->partials, kPartBlocks, h->stream);
+            nrec = launch_defect(L, x, h->beta, h->gamma, h->diag, h->W, h->ib, h->rho, h->dlt,
+                                 h->partials, h->stream);
         else
             nrec = launch_residual(L, x, h->beta, h->gamma, h->diag, h->W, h->partials,
                                    h->stream);
@@ -385,8 +385,8 @@ seg4d_status presmooth(seg4d *h, const float *src, float *dst, long long &sweeps
     CK_LAUNCH("smooth_coef");
     CK(cudaMemcpyAsync(dst, src, 2 * L.S * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     SolveOut so;
-    seg4d_status st = solve_system(h, dst, h->p.omega_smooth, h->p.tol_smooth, h->p.max_iters,
-                                   h->p.check_every, so);
+    seg4d_status st = solve_system(h, dst, kPartBlocks, h->p.omega_smooth, h->p.tol_smooth,
+                                   h->p.max_iters, h->p.check_every, so);
     if (st) return st;
     sweeps += so.iters;
     if (!so.converged)
@@ -463,8 +463,8 @@ seg4d_status run_setup(seg4d *h, long long &sweeps)
 // coefficients + solve on u; fills info fields of the solve
 seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
 {
-    launch_step_coef(h->L, h->u, h->G, h->p.h, h->p.tau, h->p.eps, h->beta, h->gamma, h->diag,
-                     h->W, h->partials, kPartBlocks, h->stream);
+    const int brec = launch_step_coef(h->L, h->u, h->G, h->p.h, h->p.tau, h->p.eps, h->beta,
+                                      h->gamma, h->diag, h->W, h->partials, h->stream);
     h->launches += 1;
     CK_LAUNCH("step_coef");
     h->has_coef = true;
@@ -490,7 +490,7 @@ seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
         CK_LAUNCH("mixed_prepare");
     }
     SolveOut so;
-    seg4d_status st = solve_system(h, h->u, h->p.omega, h->p.tol, h->p.max_iters,
+    seg4d_status st = solve_system(h, h->u, brec, h->p.omega, h->p.tol, h->p.max_iters,
                                    h->p.check_every, so, mixed);
     if (st) return st;
     sweeps += so.iters;

@@ -154,32 +154,47 @@ __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_bsweep(
                                row, s0, rp);
 }
 
-// residual records per chunk of kChunkTiles tiles: (sum r^2, min x, max x)
-__global__ void __launch_bounds__(256) k_bresidual(const BWin *__restrict__ wins,
-                                                   const long long *__restrict__ cstarts, int nwin,
-                                                   double *__restrict__ parts)
+// residual records per chunk of kChunkTiles tiles: (sum r^2, min x, max x),
+// r = D (ubar - x) with the sweep's gather (gather_vec); a chunk is
+// kChunkTiles / N tiles of 256 N-slot groups, both colours
+__global__ void __launch_bounds__(256, 2) k_bresidual(const BWin *__restrict__ wins,
+                                                      const long long *__restrict__ cstarts,
+                                                      int nwin, double *__restrict__ parts)
 {
+    constexpr int N = kVecF32;
     const long long b = blockIdx.x;
     const int w = find_win(cstarts, nwin, b);
     const Layout L = wins[w].L;
     const float *x = wins[w].x, *beta = wins[w].beta, *gamma = wins[w].gamma;
     const float *diag = wins[w].diag, *W = wins[w].W;
-    const long long nt = win_tiles(L);
-    const long long t0 = (b - cstarts[w]) * kChunkTiles;
+    const long long nt = win_gtiles(L, N);
+    const long long t0 = (b - cstarts[w]) * (kChunkTiles / N);
     Rec3f a = rec3f_init();
-    for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
-        RowPos rp;
-        int s, row;
-        if (!tile_pos(wins[w], t, rp, s, row)) continue;
-        const long long q = (long long)row * L.P + s;
+    for (long long t = t0; t < t0 + kChunkTiles / N && t < nt; ++t) {
+        RowPos rp{0, 0, 0, 0};
+        int s0 = 0, row = 0;
+        const bool in_win = group_pos<N>(wins[w], t, rp, s0, row);
         for (int C = 0; C < 2; ++C) {
-            if (2 * s + (C ^ rp.p) >= L.n1) continue;
-            const float acc = C ? neighbour_sum<1>(L, x, W, row, s, rp)
-                                : neighbour_sum<0>(L, x + L.S, W, row, s, rp);
-            const float u = x[C * L.S + q];
-            const float ubar = __fmaf_rn(gamma[C * L.S + q], acc, beta[C * L.S + q]);
-            const float r = __fmul_rn(diag[C * L.S + q], __fsub_rn(ubar, u));
-            rec3f_add(a, __fmul_rn(r, r), u);
+            const bool act = in_win && 2 * s0 + (C ^ rp.p) < L.n1;
+            const long long q = (long long)row * L.P + s0 + (C ? L.S : 0);
+            float xs[N], bp[N], gp[N], dp[N], acc[N];
+            ldv<N>(xs, act, x + q);
+            ldv<N>(bp, act, beta + q);
+            ldv<N>(gp, act, gamma + q);
+            ldv<N>(dp, act, diag + q);
+            if (C)
+                gather_vec<1, float, N>(L, x, W, act, row, s0, rp, acc);
+            else
+                gather_vec<0, float, N>(L, x, W, act, row, s0, rp, acc);
+            if (!act) continue;
+            const int e = C ^ rp.p;
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                if (2 * (s0 + m) + e >= L.n1) continue;
+                const float ubar = __fmaf_rn(gp[m], acc[m], bp[m]);
+                const float r = __fmul_rn(dp[m], __fsub_rn(ubar, xs[m]));
+                rec3f_add(a, __fmul_rn(r, r), xs[m]);
+            }
         }
     }
     block_write3(rec3f_acc(a), parts + 3 * b);
@@ -197,10 +212,12 @@ __global__ void __launch_bounds__(256) k_breduce(const long long *__restrict__ c
     block_write3(a, out + 3 * w);
 }
 
-// step coefficients (Eq. new1) for every window; records (sum b^2, min, max)
-__global__ void __launch_bounds__(256) k_bcoef(const BWin *__restrict__ wins,
-                                               const long long *__restrict__ cstarts, int nwin,
-                                               StepConst K, double *__restrict__ parts)
+// step coefficients (coef_finish, Eq. new1) for every window, one voxel per
+// lane on the window's linear 256-slot tiles (coef_gather); records
+// (sum b^2, min, max)
+__global__ void __launch_bounds__(256, 2) k_bcoef(const BWin *__restrict__ wins,
+                                                  const long long *__restrict__ cstarts, int nwin,
+                                                  StepConst K, double *__restrict__ parts)
 {
     const long long b = blockIdx.x;
     const int w = find_win(cstarts, nwin, b);
@@ -211,34 +228,31 @@ __global__ void __launch_bounds__(256) k_bcoef(const BWin *__restrict__ wins,
     const long long t0 = (b - cstarts[w]) * kChunkTiles;
     Rec3f a = rec3f_init();
     for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
-        RowPos rp;
-        int s, row;
-        if (!tile_pos(wins[w], t, rp, s, row)) continue;
+        RowPos rp{0, 0, 0, 0};
+        int s = 0, row = 0;
+        const bool in_win = tile_pos(wins[w], t, rp, s, row);
         const long long q = (long long)row * L.P + s;
         for (int C = 0; C < 2; ++C) {
-            const int i = 2 * s + (C ^ rp.p);
-            if (i >= L.n1) continue;
-            float g2[8];
-            face_grad_sq8(L, u, i, rp.j, rp.k, rp.l, K.inv_h, g2);
-            float sum = 0.0f;
+            const bool act = in_win && 2 * s + (C ^ rp.p) < L.n1;
+            float g[8];
 #pragma unroll
-            for (int f = 0; f < 8; ++f) sum += g2[f];
-            const float Abar = sqrtf(K.eps2 + 0.125f * sum);
-            const float cc = K.tau * Abar;
-            float wsum = 0.0f;
+            for (int f = 0; f < 8; ++f)
+                g[f] = act ? G[((long long)C * 8 + f) * L.S + q] : 0.0f;
+            float u0, sm[4], sp[4], ed[6][2][2];
+            if (C)
+                coef_gather<1>(L, u, act, row, s, rp, u0, sm, sp, ed);
+            else
+                coef_gather<0>(L, u, act, row, s, rp, u0, sm, sp, ed);
+            if (!act) continue;
+            float wf[8], D, bt, gm;
+            coef_finish(K, g, u0, sm, sp, ed, wf, D, bt, gm);
+            if (C == 0)
 #pragma unroll
-            for (int f = 0; f < 8; ++f) {
-                const float Af = sqrtf(K.eps2 + g2[f]);
-                const float wf = G[((long long)C * 8 + f) * L.S + q] / Af * K.inv_h2[f >> 1];
-                wsum += wf;
-                if (C == 0) W[(long long)f * L.S + q] = wf;
-            }
-            const float D = 1.0f + cc * wsum;
-            const float bv = u[C * L.S + q];
+                for (int f = 0; f < 8; ++f) W[(long long)f * L.S + q] = wf[f];
             diag[C * L.S + q] = D;
-            beta[C * L.S + q] = bv / D;
-            gamma[C * L.S + q] = cc / D;
-            rec3f_add(a, __fmul_rn(bv, bv), bv);
+            beta[C * L.S + q] = bt;
+            gamma[C * L.S + q] = gm;
+            rec3f_add(a, __fmul_rn(u0, u0), u0);
         }
     }
     block_write3(rec3f_acc(a), parts + 3 * b);
@@ -327,34 +341,54 @@ __global__ void __launch_bounds__(256) k_bmixed_prepare(const BWin *__restrict__
     }
 }
 
-// exact residual in flux form (records) + rho = r / D_b, delta = 0; beta
-// holds b itself after k_bmixed_prepare
-__global__ void __launch_bounds__(256) k_bdefect(const BWin *__restrict__ wins,
-                                                 const long long *__restrict__ cstarts, int nwin,
-                                                 double *__restrict__ parts)
+// exact residual in flux form (flux_residual_vec; records) + rho = r / D_b,
+// delta = 0; beta holds b itself after k_bmixed_prepare.  A chunk of
+// kChunkTiles 256-slot tiles is kChunkTiles / N tiles of 256 N-slot groups.
+__global__ void __launch_bounds__(256, 2) k_bdefect(const BWin *__restrict__ wins,
+                                                    const long long *__restrict__ cstarts,
+                                                    int nwin, double *__restrict__ parts)
 {
+    constexpr int N = kVecF32;
     const long long b = blockIdx.x;
     const int w = find_win(cstarts, nwin, b);
     const Layout L = wins[w].L;
     const float *x = wins[w].x, *beta = wins[w].beta, *gamma = wins[w].gamma;
     const float *diag = wins[w].diag, *W = wins[w].W, *ib = wins[w].ib;
     float *rho = wins[w].rho, *dlt = wins[w].dlt;
-    const long long nt = win_tiles(L);
-    const long long t0 = (b - cstarts[w]) * kChunkTiles;
+    const long long nt = win_gtiles(L, N);
+    const long long t0 = (b - cstarts[w]) * (kChunkTiles / N);
     Rec3f a = rec3f_init();
-    for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
-        RowPos rp;
-        int s, row;
-        if (!tile_pos(wins[w], t, rp, s, row)) continue;
-        const long long q = (long long)row * L.P + s;
+    for (long long t = t0; t < t0 + kChunkTiles / N && t < nt; ++t) {
+        RowPos rp{0, 0, 0, 0};
+        int s0 = 0, row = 0;
+        const bool in_win = group_pos<N>(wins[w], t, rp, s0, row);
         for (int C = 0; C < 2; ++C) {
-            if (2 * s + (C ^ rp.p) >= L.n1) continue;
-            float u;
-            const float r = C ? flux_residual<1>(L, x, beta, gamma, diag, W, row, s, rp, u)
-                              : flux_residual<0>(L, x, beta, gamma, diag, W, row, s, rp, u);
-            rho[C * L.S + q] = r * ib[C * L.S + q];
-            dlt[C * L.S + q] = 0.0f;
-            rec3f_add(a, __fmul_rn(r, r), u);
+            const bool act = in_win && 2 * s0 + (C ^ rp.p) < L.n1;
+            const long long q = (long long)row * L.P + s0 + (C ? L.S : 0);
+            float xs[N], bv[N], gm[N], dg[N], iv[N], res[N];
+            ldv<N>(xs, act, x + q);
+            ldv<N>(bv, act, beta + q);
+            ldv<N>(gm, act, gamma + q);
+            ldv<N>(dg, act, diag + q);
+            ldv<N>(iv, act, ib + q);
+            if (C)
+                flux_residual_vec<1, N>(L, x, W, act, row, s0, rp, xs, bv, gm, dg, res);
+            else
+                flux_residual_vec<0, N>(L, x, W, act, row, s0, rp, xs, bv, gm, dg, res);
+            if (!act) continue;
+            const int e = C ^ rp.p;
+            float rh[N], zero[N];
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                zero[m] = 0.0f;
+                rh[m] = 0.0f;
+                if (2 * (s0 + m) + e < L.n1) {
+                    rh[m] = __fmul_rn(res[m], iv[m]);
+                    rec3f_add(a, __fmul_rn(res[m], res[m]), xs[m]);
+                }
+            }
+            stv<N>(rho + q, rh);
+            stv<N>(dlt + q, zero);
         }
     }
     block_write3(rec3f_acc(a), parts + 3 * b);

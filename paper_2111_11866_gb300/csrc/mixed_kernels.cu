@@ -70,31 +70,66 @@ __global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__
     })
 }
 
-// Defect pass: r for every voxel; rho = r / D_b, delta = 0; records
-// (sum r^2, min u, max u) in FP64.  b is the prepared beta array.
-__global__ void __launch_bounds__(kPartThreads) k_defect(Layout L, const float *__restrict__ u,
-                                                         const float *__restrict__ b,
-                                                         const float *__restrict__ gamma,
-                                                         const float *__restrict__ diag,
-                                                         const float *__restrict__ W,
-                                                         const float *__restrict__ ib,
-                                                         float *__restrict__ rho,
-                                                         float *__restrict__ delta,
-                                                         double *__restrict__ partials)
+// Defect pass: the exact residual r of every voxel in flux form
+// (flux_residual_vec); rho = r / D_b, delta = 0; records (sum r^2, min u,
+// max u).  b is the prepared beta array.  Work items and grid as the
+// residual kernel: item t = 2 * tile + colour over the sweep's tiles.
+template <int N>
+__global__ void __launch_bounds__(256, 2) k_defect(Layout L, const float *__restrict__ u,
+                                                   const float *__restrict__ b,
+                                                   const float *__restrict__ gamma,
+                                                   const float *__restrict__ diag,
+                                                   const float *__restrict__ W,
+                                                   const float *__restrict__ ib,
+                                                   float *__restrict__ rho,
+                                                   float *__restrict__ delta,
+                                                   double *__restrict__ partials)
 {
+    const int nch = (L.P + 32 * N - 1) / (32 * N);
+    const long long items = 2LL * nch * L.njb * L.n3 * L.n4;
     Rec3f a = rec3f_init();
-    MX_FOR_TILES(L, s, rp, row, {
-        const long long q = (long long)row * L.P + s;
-        for (int C = 0; C < 2; ++C) {
-            if (2 * s + (C ^ rp.p) >= L.n1) continue;
-            float uv;
-            const float r = C ? flux_residual<1>(L, u, b, gamma, diag, W, row, s, rp, uv)
-                              : flux_residual<0>(L, u, b, gamma, diag, W, row, s, rp, uv);
-            rho[C * L.S + q] = r * ib[C * L.S + q];
-            delta[C * L.S + q] = 0.0f;
-            rec3f_add(a, __fmul_rn(r, r), uv);
+    for (long long t = blockIdx.x; t < items; t += gridDim.x) {
+        const int C = (int)(t & 1);
+        long long r = t >> 1;
+        const int chunk = (int)(r % nch);
+        r /= nch;
+        const int jb = (int)(r % L.njb);
+        r /= L.njb;
+        RowPos rp;
+        rp.k = (int)(r % L.n3);
+        rp.l = (int)(r / L.n3);
+        rp.j = jb * 8 + (int)(threadIdx.x >> 5);
+        rp.p = (rp.j + rp.k + rp.l) & 1;
+        const int s0 = chunk * 32 * N + N * (int)(threadIdx.x & 31);
+        if (rp.j >= L.n2) continue;   // the whole warp
+        const bool act = s0 < L.P && 2 * s0 + (C ^ rp.p) < L.n1;
+        const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
+        const long long q = (long long)row * L.P + s0 + (C ? L.S : 0);
+        float xs[N], bv[N], gm[N], dg[N], iv[N], res[N];
+        ldv<N>(xs, act, u + q);
+        ldv<N>(bv, act, b + q);
+        ldv<N>(gm, act, gamma + q);
+        ldv<N>(dg, act, diag + q);
+        ldv<N>(iv, act, ib + q);
+        if (C)
+            flux_residual_vec<1, N>(L, u, W, act, row, s0, rp, xs, bv, gm, dg, res);
+        else
+            flux_residual_vec<0, N>(L, u, W, act, row, s0, rp, xs, bv, gm, dg, res);
+        if (!act) continue;
+        const int e = C ^ rp.p;
+        float rh[N], zero[N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            zero[m] = 0.0f;
+            rh[m] = 0.0f;
+            if (2 * (s0 + m) + e < L.n1) {
+                rh[m] = __fmul_rn(res[m], iv[m]);
+                rec3f_add(a, __fmul_rn(res[m], res[m]), xs[m]);
+            }
         }
-    })
+        stv<N>(rho + q, rh);
+        stv<N>(delta + q, zero);
+    }
     block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
 }
 
@@ -122,11 +157,15 @@ void launch_mixed_prepare(const Layout &L, const float *u, const float *W, const
                                                  beta);
 }
 
-void launch_defect(const Layout &L, const float *u, const float *b, const float *gamma,
-                   const float *diag, const float *W, const float *ib, float *rho, float *delta,
-                   double *partials, int nparts, cudaStream_t st)
+int launch_defect(const Layout &L, const float *u, const float *b, const float *gamma,
+                  const float *diag, const float *W, const float *ib, float *rho, float *delta,
+                  double *partials, cudaStream_t st)
 {
-    k_defect<<<nparts, kPartThreads, 0, st>>>(L, u, b, gamma, diag, W, ib, rho, delta, partials);
+    const int N = kVecF32;
+    const long long items = 2LL * ((L.P + 32 * N - 1) / (32 * N)) * L.njb * L.n3 * L.n4;
+    const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
+    k_defect<kVecF32><<<blocks, 256, 0, st>>>(L, u, b, gamma, diag, W, ib, rho, delta, partials);
+    return blocks;
 }
 
 void launch_apply(const Layout &L, float *u, const float *delta, cudaStream_t st)

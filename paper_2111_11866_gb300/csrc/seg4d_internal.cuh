@@ -117,9 +117,10 @@ void launch_smooth_coef(const Layout &L, const float *I, const double *h, double
                         int nparts, cudaStream_t st);
 
 // step and solve (solve_kernels.cu)
-void launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,
-                      double tau, double eps, float *beta, float *gamma, float *diag, float *W,
-                      double *partials, int nparts, cudaStream_t st);
+// returns the number of per-block records (sum b^2, min b, max b) written
+int launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,
+                     double tau, double eps, float *beta, float *gamma, float *diag, float *W,
+                     double *partials, cudaStream_t st);
 void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,
                   const float *W, float omega, cudaStream_t st);
 void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta,
@@ -130,9 +131,10 @@ void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta
 void launch_mixed_prepare(const Layout &L, const float *u, const float *W, const float *gamma,
                           const float *diag, void *Wb, float *gb, float *ib, float *beta,
                           cudaStream_t st);
-void launch_defect(const Layout &L, const float *u, const float *b, const float *gamma,
-                   const float *diag, const float *W, const float *ib, float *rho, float *delta,
-                   double *partials, int nparts, cudaStream_t st);
+// returns the number of per-block records written to `partials`
+int launch_defect(const Layout &L, const float *u, const float *b, const float *gamma,
+                  const float *diag, const float *W, const float *ib, float *rho, float *delta,
+                  double *partials, cudaStream_t st);
 // red-black SOR on the BF16 correction system A_b delta = r (solve_kernels.cu)
 void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *rho,
                         const float *gb, const void *Wb, float omega, cudaStream_t st);

@@ -379,56 +379,63 @@ void launch_reduce_partials(const double *partials, int nparts, double *out, cud
     k_reduce<<<1, 1024, 0, st>>>(partials, nparts, out);
 }
 
-// Coefficients of the step system from u = u^{resc,n-1} (also b):
-//   A_f = sqrt(eps^2 + |grad^f u|^2), Abar = sqrt(eps^2 + (1/8) sum_f |grad^f u|^2)
-//   w_f = G_f / (A_f h_d^2), c = tau * Abar, D = 1 + c sum_f w_f      (Eq. new1)
-//   beta = b / D, gamma = c / D.
-// Red voxels store their 8 w_f.  Records: (sum b^2, min b, max b).
-__global__ void __launch_bounds__(kPartThreads) k_step_coef(Layout L, const float *__restrict__ u,
-                                                            const float *__restrict__ G,
-                                                            StepConst K, float *__restrict__ beta,
-                                                            float *__restrict__ gamma,
-                                                            float *__restrict__ diag,
-                                                            float *__restrict__ W,
-                                                            double *__restrict__ partials)
+// Coefficients of the step system (coef_finish, Eq. new1) from
+// u = u^{resc,n-1} (also b).  Red voxels store their 8 w_f.  Records: (sum b^2, min b, max b).  Work
+// item t = 2 * tile + colour, tile = 32 slots x 8 rows at one (k, l), one
+// voxel per lane (coef_gather); blocks stride over the items.
+__global__ void __launch_bounds__(256, 2) k_step_coef(Layout L, const float *__restrict__ u,
+                                                      const float *__restrict__ G, StepConst K,
+                                                      float *__restrict__ beta,
+                                                      float *__restrict__ gamma,
+                                                      float *__restrict__ diag,
+                                                      float *__restrict__ W,
+                                                      double *__restrict__ partials)
 {
+    const long long items = 2LL * L.nchunk * L.njb * L.n3 * L.n4;
     Rec3f a = rec3f_init();
-    FOR_TILES(L, s, rp, row, {
+    for (long long t = blockIdx.x; t < items; t += gridDim.x) {
+        const int C = (int)(t & 1);
+        long long r = t >> 1;
+        const int chunk = (int)(r % L.nchunk);
+        r /= L.nchunk;
+        const int jb = (int)(r % L.njb);
+        r /= L.njb;
+        RowPos rp;
+        rp.k = (int)(r % L.n3);
+        rp.l = (int)(r / L.n3);
+        rp.j = jb * 8 + (int)(threadIdx.x >> 5);
+        if (rp.j >= L.n2) continue;   // the whole warp
+        rp.p = (rp.j + rp.k + rp.l) & 1;
+        const int s = chunk * 32 + (int)(threadIdx.x & 31);
+        const bool act = s < L.P && 2 * s + (C ^ rp.p) < L.n1;
+        const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
         const long long q = (long long)row * L.P + s;
-        _Pragma("unroll 1")
-        for (int C = 0; C < 2; ++C) {
-            const int i = 2 * s + (C ^ rp.p);
-            if (i < L.n1) {
-                float g2[8];
-                face_grad_sq8(L, u, i, rp.j, rp.k, rp.l, K.inv_h, g2);
-                float sum = 0.0f;
-                _Pragma("unroll")
-                for (int f = 0; f < 8; ++f) sum += g2[f];
-                const float Abar = sqrtf(K.eps2 + 0.125f * sum);
-                const float cc = K.tau * Abar;
-                float wsum = 0.0f;
-                _Pragma("unroll")
-                for (int f = 0; f < 8; ++f) {
-                    const float Af = sqrtf(K.eps2 + g2[f]);
-                    const float w = G[((long long)C * 8 + f) * L.S + q] / Af * K.inv_h2[f >> 1];
-                    wsum += w;
-                    if (C == 0) W[(long long)f * L.S + q] = w;
-                }
-                const float D = 1.0f + cc * wsum;
-                const float b = u[C * L.S + q];
-                diag[C * L.S + q] = D;
-                beta[C * L.S + q] = b / D;
-                gamma[C * L.S + q] = cc / D;
-                rec3f_add(a, __fmul_rn(b, b), b);
-            }
-        }
-    })
+        float g[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) g[f] = act ? G[((long long)C * 8 + f) * L.S + q] : 0.0f;
+        float u0, sm[4], sp[4], ed[6][2][2];
+        if (C)
+            coef_gather<1>(L, u, act, row, s, rp, u0, sm, sp, ed);
+        else
+            coef_gather<0>(L, u, act, row, s, rp, u0, sm, sp, ed);
+        if (!act) continue;
+        float w[8], D, bt, gm;
+        coef_finish(K, g, u0, sm, sp, ed, w, D, bt, gm);
+        const long long qc = (long long)C * L.S + q;
+        if (C == 0)
+#pragma unroll
+            for (int f = 0; f < 8; ++f) W[(long long)f * L.S + q] = w[f];
+        diag[qc] = D;
+        beta[qc] = bt;
+        gamma[qc] = gm;
+        rec3f_add(a, __fmul_rn(u0, u0), u0);
+    }
     block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
 }
 
-void launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,
-                      double tau, double eps, float *beta, float *gamma, float *diag, float *W,
-                      double *partials, int nparts, cudaStream_t st)
+int launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,
+                     double tau, double eps, float *beta, float *gamma, float *diag, float *W,
+                     double *partials, cudaStream_t st)
 {
     StepConst K;
     for (int d = 0; d < 4; ++d) {
@@ -437,7 +444,10 @@ void launch_step_coef(const Layout &L, const float *u, const float *G, const dou
     }
     K.tau = (float)tau;
     K.eps2 = (float)(eps * eps);
-    k_step_coef<<<nparts, kPartThreads, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials);
+    const long long items = 2LL * L.nchunk * L.njb * L.n3 * L.n4;
+    const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
+    k_step_coef<<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials);
+    return blocks;
 }
 
 }  // namespace seg4d_impl

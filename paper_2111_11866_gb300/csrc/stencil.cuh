@@ -199,22 +199,25 @@ __device__ __forceinline__ void stv(float *p, const float (&v)[N])
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// Neighbour sums of the N voxels in slots s0 .. s0+N-1 (s0 a multiple of N)
-// of colour C in row `row`: acc[m] = sum_f w_f x_nb(f) with the arithmetic
-// of neighbour_sum (products rounded, fixed addition tree, a face outside
-// the grid contributes exactly 0).  x is the [2][S] iterate, W the [8][S]
-// face weights by red end (FP32, or BF16 widened exactly).  Every load is an
-// N-wide vector load, all issued before any is used; a caller that needs
-// more per-voxel data issues those loads before calling, so that they are in
-// flight together.  The x-neighbour just past either end of the group (and,
-// for black voxels, its face weight) comes from the adjacent lane by shuffle
-// when that lane holds the adjacent group of the same row, and is loaded
-// otherwise.  All 32 lanes of the warp must call this; lanes without a group
-// pass act = false (their acc is not set).
-template <int C, typename WT, int N>
-__device__ __forceinline__ void gather_vec(const Layout &L, const float *__restrict__ x,
-                                           const WT *__restrict__ W, bool act, int row, int s0,
-                                           const RowPos &rp, float (&acc)[N])
+// Loads and lane shuffles shared by the group kernels: for the N voxels in
+// slots s0 .. s0+N-1 (s0 a multiple of N) of colour C in row `row`, calls
+// fn(m, xm, xp, wm, wp, inm, inp, a, y, in) per voxel m with its -x / +x
+// neighbour values and weights (inm / inp: that neighbour slot exists) and
+// the y, z, t faces f = 0..5 (a[f][m] weight, y[f][m] neighbour value, in[f]
+// face inside the grid).  x is the [2][S] iterate, W the [8][S] face weights
+// by red end (FP32, or BF16 widened exactly).  Every load is an N-wide vector
+// load, all issued before any is used; a caller that needs more per-voxel
+// data issues those loads before calling, so that they are in flight
+// together.  The x-neighbour just past either end of the group (and, for
+// black voxels, its face weight) comes from the adjacent lane by shuffle when
+// that lane holds the adjacent group of the same row, and is loaded
+// otherwise.  kAllW (red only): also load the weights of faces outside the
+// grid (a red voxel owns them).  All 32 lanes of the warp must call this;
+// lanes without a group pass act = false (fn is not called).
+template <int C, typename WT, int N, bool kAllW, typename Fn>
+__device__ __forceinline__ void gather_core(const Layout &L, const float *__restrict__ x,
+                                            const WT *__restrict__ W, bool act, int row, int s0,
+                                            const RowPos &rp, Fn fn)
 {
     const long long S = L.S;
     const long long q = (long long)row * L.P + s0;
@@ -236,7 +239,7 @@ __device__ __forceinline__ void gather_vec(const Layout &L, const float *__restr
         // red: own face f+2; black: the opposite face of the red neighbour
         const long long wi = C == 0 ? (long long)(f + 2) * S + q
                                     : (long long)((f + 2) ^ 1) * S + q + off[f];
-        ldv<N>(a[f], in[f], W + wi);
+        ldv<N>(a[f], (kAllW && C == 0) ? act : in[f], W + wi);
         ldv<N>(y[f], in[f], xo + q + off[f]);
     }
     const unsigned key = act ? (unsigned)q : 0xFFFFFFFFu;   // q is even; the sentinel odd
@@ -273,14 +276,83 @@ __device__ __forceinline__ void gather_vec(const Layout &L, const float *__restr
         }
         const bool inm = e == 1 || m > 0 || hasL;
         const bool inp = e == 0 || m < N - 1 || hasR;
-        acc[m] = sum8(inm ? __fmul_rn(wm, xm) : 0.0f, inp ? __fmul_rn(wp, xp) : 0.0f,
-                      in[0] ? __fmul_rn(a[0][m], y[0][m]) : 0.0f,
-                      in[1] ? __fmul_rn(a[1][m], y[1][m]) : 0.0f,
-                      in[2] ? __fmul_rn(a[2][m], y[2][m]) : 0.0f,
-                      in[3] ? __fmul_rn(a[3][m], y[3][m]) : 0.0f,
-                      in[4] ? __fmul_rn(a[4][m], y[4][m]) : 0.0f,
-                      in[5] ? __fmul_rn(a[5][m], y[5][m]) : 0.0f);
+        fn(m, xm, xp, wm, wp, inm, inp, a, y, in);
     }
+}
+
+// Neighbour sums acc[m] = sum_f w_f x_nb(f) of a group (see gather_core),
+// with the arithmetic of neighbour_sum (products rounded, fixed addition
+// tree, a face outside the grid contributes exactly 0).
+template <int C, typename WT, int N>
+__device__ __forceinline__ void gather_vec(const Layout &L, const float *__restrict__ x,
+                                           const WT *__restrict__ W, bool act, int row, int s0,
+                                           const RowPos &rp, float (&acc)[N])
+{
+    gather_core<C, WT, N, false>(
+        L, x, W, act, row, s0, rp,
+        [&](int m, float xm, float xp, float wm, float wp, bool inm, bool inp,
+            const float (&a)[6][N], const float (&y)[6][N], const bool (&in)[6]) {
+            acc[m] = sum8(inm ? __fmul_rn(wm, xm) : 0.0f, inp ? __fmul_rn(wp, xp) : 0.0f,
+                          in[0] ? __fmul_rn(a[0][m], y[0][m]) : 0.0f,
+                          in[1] ? __fmul_rn(a[1][m], y[1][m]) : 0.0f,
+                          in[2] ? __fmul_rn(a[2][m], y[2][m]) : 0.0f,
+                          in[3] ? __fmul_rn(a[3][m], y[3][m]) : 0.0f,
+                          in[4] ? __fmul_rn(a[4][m], y[4][m]) : 0.0f,
+                          in[5] ? __fmul_rn(a[5][m], y[5][m]) : 0.0f);
+        });
+}
+
+// Exact residual of the step system in flux form for the N voxels of a
+// group (see gather_core), FP32 weights:
+//   r = (b - u) - c (sum_f w_f (u - u_nb) + u * w_bnd),   c = gamma * D,
+// the same A u as D u - c sum_f w_f u_nb, but the differences u - u_nb are
+// small and exact, so r carries far less rounding noise than D (ubar - u).
+// Faces to an existing slot enter the flux (a padding slot holds 0, so a
+// face to it contributes w u, as a boundary face does); w_bnd collects the
+// rest.  A red voxel owns all its weights; a black voxel's boundary weights
+// are stored nowhere, so for a black voxel on the grid boundary w_bnd =
+// (D - 1)/c - (sum of the weights in the flux), and 0 elsewhere.  xs, b,
+// gm, dg: the group's u, b, gamma, D, loaded by the caller before the call.
+template <int C, int N>
+__device__ __forceinline__ void flux_residual_vec(const Layout &L, const float *__restrict__ x,
+                                                  const float *__restrict__ W, bool act, int row,
+                                                  int s0, const RowPos &rp,
+                                                  const float (&xs)[N], const float (&b)[N],
+                                                  const float (&gm)[N], const float (&dg)[N],
+                                                  float (&r)[N])
+{
+    const int e = C ^ rp.p;
+    gather_core<C, float, N, true>(
+        L, x, W, act, row, s0, rp,
+        [&](int m, float xm, float xp, float wm, float wp, bool inm, bool inp,
+            const float (&a)[6][N], const float (&y)[6][N], const bool (&in)[6]) {
+            const float u = xs[m];
+            const float flux = sum8(inm ? __fmul_rn(wm, __fsub_rn(u, xm)) : 0.0f,
+                                    inp ? __fmul_rn(wp, __fsub_rn(u, xp)) : 0.0f,
+                                    in[0] ? __fmul_rn(a[0][m], __fsub_rn(u, y[0][m])) : 0.0f,
+                                    in[1] ? __fmul_rn(a[1][m], __fsub_rn(u, y[1][m])) : 0.0f,
+                                    in[2] ? __fmul_rn(a[2][m], __fsub_rn(u, y[2][m])) : 0.0f,
+                                    in[3] ? __fmul_rn(a[3][m], __fsub_rn(u, y[3][m])) : 0.0f,
+                                    in[4] ? __fmul_rn(a[4][m], __fsub_rn(u, y[4][m])) : 0.0f,
+                                    in[5] ? __fmul_rn(a[5][m], __fsub_rn(u, y[5][m])) : 0.0f);
+            const float c = __fmul_rn(gm[m], dg[m]);
+            float wb;
+            if (C == 0) {
+                wb = sum8(inm ? 0.0f : wm, inp ? 0.0f : wp, in[0] ? 0.0f : a[0][m],
+                          in[1] ? 0.0f : a[1][m], in[2] ? 0.0f : a[2][m], in[3] ? 0.0f : a[3][m],
+                          in[4] ? 0.0f : a[4][m], in[5] ? 0.0f : a[5][m]);
+            } else {
+                const int i = 2 * (s0 + m) + e;
+                const bool bnd = i == 0 || i + 1 == L.n1 || !(in[0] && in[1] && in[2] && in[3] &&
+                                                              in[4] && in[5]);
+                const float wint = sum8(inm ? wm : 0.0f, inp ? wp : 0.0f, in[0] ? a[0][m] : 0.0f,
+                                        in[1] ? a[1][m] : 0.0f, in[2] ? a[2][m] : 0.0f,
+                                        in[3] ? a[3][m] : 0.0f, in[4] ? a[4][m] : 0.0f,
+                                        in[5] ? a[5][m] : 0.0f);
+                wb = bnd ? __fsub_rn(__fdiv_rn(__fsub_rn(dg[m], 1.0f), c), wint) : 0.0f;
+            }
+            r[m] = __fsub_rn(__fsub_rn(b[m], u), __fmul_rn(c, __fmaf_rn(u, wb, flux)));
+        });
 }
 
 // One colour-C relaxation of the N voxels of a group (see gather_vec):
@@ -351,41 +423,31 @@ struct StepConst {
 // The normal component of face (d, +-) is (u(+-e_d) - u)/h_d.  Its tangential
 // component along t is the difference of the two diamond-point values,
 //   (1/4) [ (u(+e_t) - u(-e_t)) + (u(+-e_d+e_t) - u(+-e_d-e_t)) ] / h_t.
-// The centre and its 8 face neighbours are loaded once; each unordered axis
-// pair (d, t) then loads its 4 edge neighbours u(+-e_d +-e_t), which serve the
-// t-component of both d-faces and the d-component of both t-faces.
-__device__ inline void face_grad_sq8(const Layout &L, const float *__restrict__ u, int i, int j,
-                                     int k, int l, const float *inv_h, float g2[8])
+// Each unordered axis pair (d, t) has 4 edge neighbours u(+-e_d +-e_t), which
+// serve the t-component of both d-faces and the d-component of both t-faces.
+//
+// |grad^f u|^2 of the 8 faces from gathered values: u0 = u(x), sm[d] / sp[d]
+// = u(x -+ e_d), ed[pi][a][b] = u(x + (a ? 1 : -1) e_d + (b ? 1 : -1) e_t)
+// for the axis pairs pi = (d, t), d < t, in the order (0,1) (0,2) (0,3)
+// (1,2) (1,3) (2,3).
+__device__ __forceinline__ void face_grad_sq8_from(float u0, const float (&sm)[4],
+                                                   const float (&sp)[4],
+                                                   const float (&ed)[6][2][2],
+                                                   const float *inv_h, float g2[8])
 {
-    const int c[4] = {i, j, k, l};
-    const float u0 = ld_dirichlet(L, u, i, j, k, l);
-    float sm[4], sp[4];   // u(-e_d), u(+e_d)
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
-        int a[4] = {c[0], c[1], c[2], c[3]};
-        a[d] -= 1;
-        sm[d] = ld_dirichlet(L, u, a[0], a[1], a[2], a[3]);
-        a[d] += 2;
-        sp[d] = ld_dirichlet(L, u, a[0], a[1], a[2], a[3]);
         const float nm = (sm[d] - u0) * inv_h[d];
         const float np = (sp[d] - u0) * inv_h[d];
         g2[2 * d] = nm * nm;
         g2[2 * d + 1] = np * np;
     }
+    int pi = 0;
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
 #pragma unroll
-        for (int t = d + 1; t < 4; ++t) {
-            float e[2][2];   // e[sd][st] = u(x + sd' e_d + st' e_t), index 0 = -1, 1 = +1
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    int q[4] = {c[0], c[1], c[2], c[3]};
-                    q[d] += a ? 1 : -1;
-                    q[t] += b ? 1 : -1;
-                    e[a][b] = ld_dirichlet(L, u, q[0], q[1], q[2], q[3]);
-                }
+        for (int t = d + 1; t < 4; ++t, ++pi) {
+            const float(&e)[2][2] = ed[pi];
             const float dt0 = sp[t] - sm[t];   // u(+e_t) - u(-e_t)
             const float dd0 = sp[d] - sm[d];   // u(+e_d) - u(-e_d)
             // faces (d, -) and (d, +): component along t
@@ -402,108 +464,124 @@ __device__ inline void face_grad_sq8(const Layout &L, const float *__restrict__ 
     }
 }
 
-// Flux form of the off-diagonal part: sum over the interior faces of
-// w_f (x_self - x_nb(f)); the differences are formed before weighting, so
-// the sum is accurate to its own size rather than to the size of x.
-// Also returns the interior weight sum.
+// The 33 values face_grad_sq8_from needs for the voxel in slot s of colour C
+// in row `row` (one voxel per lane, lanes on consecutive slots): the centre,
+// its 8 face neighbours (other colour) and its 24 edge neighbours (same
+// colour: two steps in parity), zero outside the grid.  With i = 2s + e, the
+// x-neighbours i -+ 1 of any colour-C or other-colour row are the slots
+// (s-1, s) for e = 0 and (s, s+1) for e = 1 of that row, so each row array
+// is loaded once per lane and the slot beside it comes from the adjacent
+// lane by shuffle (or a load at a warp's end).  All 32 lanes call this;
+// lanes without a voxel pass act = false.
 template <int C>
-__device__ __forceinline__ float neighbour_flux(const Layout &L, const float *__restrict__ xo,
-                                                const float *__restrict__ W, int row, int s,
-                                                const RowPos &rp, float xs, float &wint)
+__device__ __forceinline__ void coef_gather(const Layout &L, const float *__restrict__ u, bool act,
+                                            int row, int s, const RowPos &rp, float &u0,
+                                            float (&sm)[4], float (&sp)[4], float (&ed)[6][2][2])
 {
     const long long S = L.S;
-    const long long rb = (long long)row * L.P;
-    const long long q = rb + s;
+    const long long q = (long long)row * L.P + s;
+    const float *uc = u + (C ? S : 0);   // same colour
+    const float *uo = u + (C ? 0 : S);   // other colour
+    const int e = C ^ rp.p;
     const long long dy = L.P, dz = (long long)L.n2 * L.P, dt = (long long)L.n2 * L.n3 * L.P;
-    long long wi[8], xi[8];
-    bool in[8];
-    const int i = 2 * s + (C ^ rp.p);
-    in[0] = i >= 1;
-    in[1] = i + 1 < L.n1;
-    in[2] = rp.j > 0;
-    in[3] = rp.j + 1 < L.n2;
-    in[4] = rp.k > 0;
-    in[5] = rp.k + 1 < L.n3;
-    in[6] = rp.l > 0;
-    in[7] = rp.l + 1 < L.n4;
-    if (C == 0) {
-        xi[0] = rb + s - 1 + rp.p;
-        xi[1] = rb + s + rp.p;
-        for (int f = 0; f < 8; ++f) wi[f] = (long long)f * S + q;
-    } else {
-        xi[0] = rb + s - rp.p;
-        xi[1] = rb + s + 1 - rp.p;
-        wi[0] = 1 * S + xi[0];
-        wi[1] = 0 * S + xi[1];
-        wi[2] = 3 * S + q - dy;
-        wi[3] = 2 * S + q + dy;
-        wi[4] = 5 * S + q - dz;
-        wi[5] = 4 * S + q + dz;
-        wi[6] = 7 * S + q - dt;
-        wi[7] = 6 * S + q + dt;
+    const long long off[6] = {-dy, dy, -dz, dz, -dt, dt};
+    const bool in[6] = {act && rp.j > 0, act && rp.j + 1 < L.n2, act && rp.k > 0,
+                        act && rp.k + 1 < L.n3, act && rp.l > 0, act && rp.l + 1 < L.n4};
+    u0 = act ? uc[q] : 0.0f;
+    const float X = act ? uo[q] : 0.0f;
+    float nb[6], V[6], dg[3][2][2];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        nb[f] = in[f] ? uo[q + off[f]] : 0.0f;   // face neighbours along y, z, t
+        V[f] = in[f] ? uc[q + off[f]] : 0.0f;    // same-colour rows of the x-edges
     }
-    xi[2] = q - dy;
-    xi[3] = q + dy;
-    xi[4] = q - dz;
-    xi[5] = q + dz;
-    xi[6] = q - dt;
-    xi[7] = q + dt;
-    float acc = 0.0f, ws = 0.0f;
+    // edge neighbours in the (y,z), (y,t), (z,t) planes: same slot
+#pragma unroll
+    for (int pp = 0; pp < 3; ++pp) {
+        const int da = pp < 2 ? 0 : 1, tb = pp == 0 ? 1 : 2;   // axes among (y, z, t)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const bool ok = in[2 * da + a] && in[2 * tb + b];
+                dg[pp][a][b] = ok ? uc[q + off[2 * da + a] + off[2 * tb + b]] : 0.0f;
+            }
+    }
+    const unsigned key = act ? (unsigned)q : 0xFFFFFFFFu;
+    const unsigned keyL = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+    const unsigned keyR = __shfl_down_sync(0xFFFFFFFFu, key, 1);
+    float XL, XR, VL[6], VR[6];
+    XL = __shfl_up_sync(0xFFFFFFFFu, X, 1);
+    XR = __shfl_down_sync(0xFFFFFFFFu, X, 1);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        VL[f] = __shfl_up_sync(0xFFFFFFFFu, V[f], 1);
+        VR[f] = __shfl_down_sync(0xFFFFFFFFu, V[f], 1);
+    }
+    if (!act) return;
+    const bool hasL = s > 0, hasR = s + 1 < L.P;
+    const bool shL = hasL && keyL == (unsigned)(q - 1);
+    const bool shR = hasR && keyR == (unsigned)(q + 1);
+    if (e == 0) {   // x -+ 1 are slots s-1, s
+        sm[0] = shL ? XL : (hasL ? uo[q - 1] : 0.0f);
+        sp[0] = X;
+    } else {        // slots s, s+1
+        sm[0] = X;
+        sp[0] = shR ? XR : (hasR ? uo[q + 1] : 0.0f);
+    }
+#pragma unroll
+    for (int d = 1; d < 4; ++d) {
+        sm[d] = nb[2 * d - 2];
+        sp[d] = nb[2 * d - 1];
+    }
+    // (x, t) edges, t = y, z, t: pairs 0, 1, 2; a = x side, b = t side
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int f = 2 * t + b;
+            if (e == 0) {
+                ed[t][0][b] = shL ? VL[f] : (hasL && in[f] ? uc[q + off[f] - 1] : 0.0f);
+                ed[t][1][b] = V[f];
+            } else {
+                ed[t][0][b] = V[f];
+                ed[t][1][b] = shR ? VR[f] : (hasR && in[f] ? uc[q + off[f] + 1] : 0.0f);
+            }
+        }
+#pragma unroll
+    for (int pp = 0; pp < 3; ++pp)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) ed[3 + pp][a][b] = dg[pp][a][b];
+}
+
+// Step coefficients of one voxel (Eq. new1) from its gathered values and
+// its 8 face edge coefficients g: A_f = sqrt(eps^2 + |grad^f u|^2),
+// Abar = sqrt(eps^2 + (1/8) sum_f |grad^f u|^2), w_f = G_f / (A_f h_d^2),
+// c = tau Abar, D = 1 + c sum_f w_f, beta = b / D, gamma = c / D (b = u0).
+__device__ __forceinline__ void coef_finish(const StepConst &K, const float (&g)[8], float u0,
+                                            const float (&sm)[4], const float (&sp)[4],
+                                            const float (&ed)[6][2][2], float (&w)[8],
+                                            float &D, float &bt, float &gm)
+{
+    float g2[8];
+    face_grad_sq8_from(u0, sm, sp, ed, K.inv_h, g2);
+    float sum = 0.0f;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) sum += g2[f];
+    const float Abar = sqrtf(K.eps2 + 0.125f * sum);
+    const float cc = K.tau * Abar;
+    float wsum = 0.0f;
 #pragma unroll
     for (int f = 0; f < 8; ++f) {
-        if (!in[f]) continue;
-        const float w = W[wi[f]];
-        acc += w * (xs - xo[xi[f]]);
-        ws += w;
+        const float Af = sqrtf(K.eps2 + g2[f]);
+        w[f] = g[f] / Af * K.inv_h2[f >> 1];
+        wsum += w[f];
     }
-    wint = ws;
-    return acc;
-}
-
-// Sum of the weights of a voxel's faces to the Dirichlet ring (0 away from
-// the boundary).  A red voxel stores all 8 of its weights; a black voxel's
-// boundary weights are stored nowhere, so their sum is (D - 1)/c minus the
-// interior sum wint.
-template <int C>
-__device__ __forceinline__ float boundary_weight(const Layout &L, const float *__restrict__ W,
-                                                 long long q, int i, const RowPos &rp, float D,
-                                                 float c, float wint)
-{
-    const bool in[8] = {i >= 1, i + 1 < L.n1, rp.j > 0, rp.j + 1 < L.n2,
-                        rp.k > 0, rp.k + 1 < L.n3, rp.l > 0, rp.l + 1 < L.n4};
-    bool bnd = false;
-#pragma unroll
-    for (int f = 0; f < 8; ++f) bnd |= !in[f];
-    if (!bnd) return 0.0f;
-    if (C == 1) return (D - 1.0f) / c - wint;
-    float sb = 0.0f;
-#pragma unroll
-    for (int f = 0; f < 8; ++f)
-        if (!in[f]) sb += W[(long long)f * L.S + q];
-    return sb;
-}
-
-// Exact residual of one voxel in flux form,
-//   r = (b - u) - c (sum_f w_f (u - u_nb) + u * boundary weights),
-// the same A u as D u - c sum_f w_f u_nb, but the differences u - u_nb are
-// small and exact, so r carries far less rounding noise than D (ubar - u) and
-// the correction sweeps do not chase it.
-template <int C>
-__device__ __forceinline__ float flux_residual(const Layout &L, const float *__restrict__ u,
-                                               const float *__restrict__ b,
-                                               const float *__restrict__ gamma,
-                                               const float *__restrict__ diag,
-                                               const float *__restrict__ W, int row, int s,
-                                               const RowPos &rp, float &uv)
-{
-    const long long q = (long long)row * L.P + s;
-    uv = u[C * L.S + q];
-    float wint;
-    const float flux = neighbour_flux<C>(L, u + (C ? 0 : L.S), W, row, s, rp, uv, wint);
-    const float D = diag[C * L.S + q];
-    const float c = gamma[C * L.S + q] * D;
-    const float wb = boundary_weight<C>(L, W, q, 2 * s + (C ^ rp.p), rp, D, c, wint);
-    return (b[C * L.S + q] - uv) - c * (flux + uv * wb);
+    D = 1.0f + cc * wsum;
+    bt = u0 / D;
+    gm = cc / D;
 }
 
 // Sum over the interior faces of (w_f - bf16(w_f)) for the voxel in slot s
