@@ -204,6 +204,60 @@ def _mixed(params):
     return pm
 
 
+def run_large(nsteps, params, local):
+    """The large full grid (512x512x128 x 48 frames, 1.61G voxels, one nucleus
+    per 40^3 voxels), built on the device, `nsteps` time steps after the
+    set-up; whole-step voxel-sweeps/s, the sweep kernel's rate and its
+    roofline fraction (algorithmic bytes, CUDA-event time)."""
+    import torch
+    from paper_2111_11866_gb300 import _lib, synth
+
+    img, seeds, _, meta = synth.large("cuda")
+    dims = tuple(reversed(img.shape))
+    nvox = img.numel()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    seg = _lib.Seg4D(dims, stream=stream, params=params)
+    try:
+        seg.set_image(img)
+        del img
+        torch.cuda.empty_cache()
+        seg.set_seeds(seeds)
+        t_setup = time.perf_counter()
+        seg.setup()
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t_setup
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = seg.step(nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        sweeps = info["sweeps_total"]
+        peak, peak_kind = _peaks()
+        rate = nvox * sweeps / (info["sweep_ms"] / 1000.0)
+        return {"workload": f"{meta['name']} ({meta['count']} nuclei), {nsteps} steps",
+                "voxels": nvox, "value": nvox * sweeps / (ms / 1000.0),
+                "unit": "voxel-sweeps/s", "ms_per_time_step": ms / nsteps,
+                "sweeps_per_time_step": sweeps / nsteps, "sweep_rate": rate,
+                "roofline": {"bound": "hbm", "kernel": SWEEP_KERNELS[params.sweep_variant],
+                             "achieved": ALG_BYTES_PER_VOXEL_SWEEP * rate / 1e9, "peak": peak,
+                             "unit": "GB/s",
+                             "frac": ALG_BYTES_PER_VOXEL_SWEEP * rate / 1e9 / peak,
+                             "peak_kind": peak_kind},
+                "last_res_rel": info["res_rel"], "setup_s": t_setup,
+                "device_gb": _lib.Seg4D.device_bytes(dims) / 1e9, "clocks": clocks,
+                "data": "synthetic, generated on the device (seeded)"}
+    finally:
+        seg.close()
+        torch.cuda.empty_cache()
+
+
 def run_batched(nwin, nsteps, params, plain_sample=48):
     """Per-nucleus windows (edge U[24,64], 8-16 frames) advanced by the batch
     engine in mixed precision (BF16 sweep weights, FP32 defect passes) with
@@ -253,12 +307,12 @@ def run_batched(nwin, nsteps, params, plain_sample=48):
             "dtype": "mixed: bf16 sweep weights, f32 sweeps and defect passes, f64 norms"}
 
 
-def run_serving(rate, seconds, budget_gb, params, pool=24, plain_sample=8):
+def run_serving(rate, seconds, budget_gb, params, pool=24):
     """Open-loop Poisson requests (window edge log-uniform 16..96, frames =
     edge/4), continuous batching under a device budget; p50/p99 latency and
-    seg/s at the offered rate, then at half the measured capacity; sequential
-    plain solves of the same windows as the comparison."""
-    import numpy as np
+    seg/s at the offered rate, the closed-loop capacity (every pool request
+    arriving at once), then p50/p99 at half that capacity.  The comparison is
+    sequential plain FP32 solves of the same pool of requests, one at a time."""
     import torch
     from paper_2111_11866_gb300 import serve, synth
     sizes = synth.request_sizes(pool)
@@ -276,24 +330,27 @@ def run_serving(rate, seconds, budget_gb, params, pool=24, plain_sample=8):
                        f"30 steps, {budget_gb:g} GB admission budget, pool of {pool} images; "
                        f"the offered rate saturates the GPU, so latency there is queueing: "
                        f"stats cover requests completed within the {seconds:g} s horizon"}
+    _plain_window(*imgs[0], params)   # warm
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k in range(plain_sample):
-        _plain_window(*imgs[k % pool], params)
+    for k in range(pool):
+        _plain_window(*imgs[k], params)
     torch.cuda.synchronize()
     tp = time.perf_counter() - t0
-    out["sequential_plain"] = {"requests": plain_sample, "seg_per_s": plain_sample / tp,
-                               "mean_ms": 1e3 * tp / plain_sample}
+    out["sequential_plain"] = {"requests": pool, "seg_per_s": pool / tp,
+                               "mean_ms": 1e3 * tp / pool}
     pm = _mixed(params)
+    with serve.Server(budget, 8192, params=pm) as srv:
+        st = srv.run([serve.Request(k, 0.0, *imgs[k % pool]) for k in range(2 * pool)])
+        cap = st.served / st.wall_s
+        out["capacity"] = {"requests": 2 * pool, "seg_per_s": cap,
+                           "speedup_vs_sequential_plain": cap * tp / pool}
     with serve.Server(budget, 8192, params=pm) as srv:
         st = srv.run(requests(rate, seconds, 11), horizon_s=seconds)
         s = st.summary()
         s["offered_rate"] = rate
         s["seg_per_s"] = st.served / seconds
         out["at_offered_rate"] = s
-    # the largest sustainable rate is what the saturated service completes
-    cap = st.served / seconds if st.served > 0 else plain_sample / tp
-    out["sustainable_rate"] = cap
     with serve.Server(budget, 8192, params=pm) as srv:
         st = srv.run(requests(0.5 * cap, seconds, 12), horizon_s=seconds + 20.0)
         s = st.summary()
@@ -317,6 +374,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="arrival horizon of the serving measurement (0 = skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--large-steps", type=int, default=20,
+                    help="time steps of the large 512x512x128x48 grid (0 = skip)")
     ap.add_argument("--sweep-variant", type=int, default=1, choices=[0, 1],
                     help="0 = fused red-black wavefront sweep, 1 = one launch per colour")
     ap.add_argument("--time-steps", type=int, default=None,
@@ -456,7 +515,9 @@ def main():
     seg.close()
     del img_d
     torch.cuda.empty_cache()
-    batched = serving = None
+    batched = serving = large = None
+    if args.large_steps > 0:
+        large = run_large(args.large_steps, params, local)
     if args.batched_windows > 0:
         batched = run_batched(args.batched_windows, args.batched_steps, params)
     if args.serve_seconds > 0:
@@ -487,6 +548,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
             "mixed_precision": mixed,
+            "large": large,
             "batched": batched,
             "serving": serving,
         }

@@ -242,6 +242,7 @@ __device__ __forceinline__ void gather_core(const Layout &L, const float *__rest
         ldv<N>(a[f], (kAllW && C == 0) ? act : in[f], W + wi);
         ldv<N>(y[f], in[f], xo + q + off[f]);
     }
+    const bool hasL = s0 > 0, hasR = s0 + N < L.P;
     const unsigned key = act ? (unsigned)q : 0xFFFFFFFFu;   // q is even; the sentinel odd
     const unsigned keyL = __shfl_up_sync(0xFFFFFFFFu, key, 1);
     const unsigned keyR = __shfl_down_sync(0xFFFFFFFFu, key, 1);
@@ -250,7 +251,6 @@ __device__ __forceinline__ void gather_core(const Layout &L, const float *__rest
     const float wLs = __shfl_up_sync(0xFFFFFFFFu, W1[N - 1], 1);
     const float wRs = __shfl_down_sync(0xFFFFFFFFu, W0[0], 1);
     if (!act) return;
-    const bool hasL = s0 > 0, hasR = s0 + N < L.P;
     const bool shL = hasL && keyL == (unsigned)(q - N);
     const bool shR = hasR && keyR == (unsigned)(q + N);
     float xl = 0.0f, xr = 0.0f, wl = 0.0f, wr = 0.0f;

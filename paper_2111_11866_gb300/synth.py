@@ -132,6 +132,64 @@ def nuclei(seed: int, n, count: int | None = None, density_per_voxel: float | No
                 {"count": count, "semi_axes": semi, "peaks": peaks, "paths": paths})
 
 
+def nuclei_device(seed: int, n, density_per_voxel: float, device, axes=(4.0, 9.0),
+                  peak=(0.5, 1.0), background: float = 0.05, photons: float = 1000.0,
+                  read_noise: float = 0.05, nsteps: int = 20, margin: float = 10.0,
+                  name: str = "nuclei (device)"):
+    """The nuclei() recipe for grids too large to build on the host: the
+    per-nucleus draws (paths, semi-axes, peaks) come from the same seeded
+    numpy generator, the image and its noise are made on `device` with a
+    seeded torch generator.  Returns (image tensor (n4, n3, n2, n1) float32 on
+    the device, seeds (m, 4), nsteps, meta)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    n1, n2, n3, n4 = n
+    count = max(1, int(round(n1 * n2 * n3 * density_per_voxel)))
+    lo = np.array([margin, margin, min(margin, n3 / 4)])
+    hi = np.array([n1 - margin, n2 - margin, n3 - min(margin, n3 / 4)])
+    paths = _trajectories(rng, count, n4, lo, hi)
+    semi = rng.uniform(axes[0], axes[1], size=(count, 3))
+    peaks = rng.uniform(peak[0], peak[1], size=count)
+    img = torch.full((n4, n3, n2, n1), background, dtype=torch.float32, device=device)
+    ar = [torch.arange(m, dtype=torch.float32, device=device) for m in (n1, n2, n3)]
+    for l in range(n4):
+        frame = img[l]
+        for a in range(count):
+            c = paths[a, l]
+            ext = 2.0 * semi[a]
+            x0, x1 = max(0, int(c[0] - ext[0])), min(n1, int(c[0] + ext[0]) + 2)
+            y0, y1 = max(0, int(c[1] - ext[1])), min(n2, int(c[1] + ext[1]) + 2)
+            z0, z1 = max(0, int(c[2] - ext[2])), min(n3, int(c[2] + ext[2]) + 2)
+            if x0 >= x1 or y0 >= y1 or z0 >= z1:
+                continue
+            rx = ((ar[0][x0:x1] - float(c[0])) / float(semi[a, 0])) ** 2
+            ry = ((ar[1][y0:y1] - float(c[1])) / float(semi[a, 1])) ** 2
+            rz = ((ar[2][z0:z1] - float(c[2])) / float(semi[a, 2])) ** 2
+            r2 = rz[:, None, None] + ry[None, :, None] + rx[None, None, :]
+            sub = frame[z0:z1, y0:y1, x0:x1]
+            torch.maximum(sub, float(peaks[a]) * torch.exp(-2.0 * r2), out=sub)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    for l in range(n4):   # noise frame by frame: bounded temporaries
+        f = img[l]
+        f.copy_(torch.poisson(f.clamp_(min=0.0) * photons, generator=g) / photons +
+                read_noise * torch.randn(f.shape, generator=g, device=device))
+    cen = np.rint(paths[:, 0, :])
+    cen[:, 0] = np.clip(cen[:, 0], 0, n1 - 1)
+    cen[:, 1] = np.clip(cen[:, 1], 0, n2 - 1)
+    cen[:, 2] = np.clip(cen[:, 2], 0, n3 - 1)
+    seeds = np.concatenate([cen, np.zeros((count, 1))], axis=1)
+    return img, seeds, nsteps, {"count": count, "name": name}
+
+
+def large(device, seed: int = 3):
+    """512x512x128 space x 48 frames (1.61G voxels), one nucleus per 40^3
+    voxels (about 524), 20 steps; built on the device (nuclei_device)."""
+    return nuclei_device(seed, (512, 512, 128, 48), 1.0 / 40 ** 3, device, nsteps=20,
+                         name="large 512x512x128x48, 1 nucleus per 40^3")
+
+
 def medium(seed: int = 2) -> Case:
     """128x128x64 space x 32 frames (33.5M voxels), 60 nuclei, 50 steps."""
     return nuclei(seed, (128, 128, 64, 32), count=60, nsteps=50,
