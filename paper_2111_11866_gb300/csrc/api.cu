@@ -120,6 +120,9 @@ bool dims_ok(const seg4d_dims *d)
     if (d->n3 > 65535 || d->n4 > 65535) return false;   // grid.y / grid.z of the sweep
     const long long rows = (long long)d->n2 * d->n3 * d->n4;
     if (rows >= (1LL << 31)) return false;
+    // work items of the tile loops (2 colours x 32-slot chunks x 8-row blocks)
+    const long long chunks = ((d->n1 + 1) / 2 + 3) / 4 * 4 / 32 + 1;
+    if (2 * chunks * ((d->n2 + 7) / 8) * d->n3 * d->n4 >= (1LL << 31)) return false;
     const long long nv = rows * d->n1;
     return nv < (1LL << 33);
 }

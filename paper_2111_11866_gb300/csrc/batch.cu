@@ -32,26 +32,6 @@ namespace seg4d_impl {
 
 constexpr int kChunkTiles = 16;   // tiles per block of the reduction kernels
 
-// Division of n < 2^31 by a runtime constant d >= 1 with a multiply-high and a
-// shift (round-up method): s = ceil(log2 d), m = ceil(2^(32+s) / d) - 2^32,
-// then n / d = (umulhi(n, m) + n) >> s; the sum stays below 2^32.
-struct FastDiv {
-    unsigned m, s, d, pad;
-};
-
-inline FastDiv make_fastdiv(unsigned d)
-{
-    unsigned s = 0;
-    while ((1ull << s) < d) ++s;
-    const unsigned long long m = ((1ull << (32 + s)) + d - 1) / d - (1ull << 32);
-    return FastDiv{(unsigned)m, s, d, 0};
-}
-
-__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f)
-{
-    return (__umulhi(n, f.m) + n) >> f.s;
-}
-
 struct BWin {
     Layout L;
     FastDiv fP, fn2, fn3;          // division by P, n2, n3

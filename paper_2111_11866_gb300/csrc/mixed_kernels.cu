@@ -83,23 +83,14 @@ __global__ void __launch_bounds__(256, 2) k_defect(Layout L, const float *__rest
                                                    const float *__restrict__ ib,
                                                    float *__restrict__ rho,
                                                    float *__restrict__ delta,
-                                                   double *__restrict__ partials)
+                                                   double *__restrict__ partials,
+                                                   ItemDecode dec, unsigned items)
 {
-    const int nch = (L.P + 32 * N - 1) / (32 * N);
-    const long long items = 2LL * nch * L.njb * L.n3 * L.n4;
     Rec3f a = rec3f_init();
-    for (long long t = blockIdx.x; t < items; t += gridDim.x) {
-        const int C = (int)(t & 1);
-        long long r = t >> 1;
-        const int chunk = (int)(r % nch);
-        r /= nch;
-        const int jb = (int)(r % L.njb);
-        r /= L.njb;
+    for (unsigned t = blockIdx.x; t < items; t += gridDim.x) {
+        int C, chunk;
         RowPos rp;
-        rp.k = (int)(r % L.n3);
-        rp.l = (int)(r / L.n3);
-        rp.j = jb * 8 + (int)(threadIdx.x >> 5);
-        rp.p = (rp.j + rp.k + rp.l) & 1;
+        decode_item(dec, L, t, (int)(threadIdx.x >> 5), C, chunk, rp);
         const int s0 = chunk * 32 * N + N * (int)(threadIdx.x & 31);
         if (rp.j >= L.n2) continue;   // the whole warp
         const bool act = s0 < L.P && 2 * s0 + (C ^ rp.p) < L.n1;
@@ -161,10 +152,11 @@ int launch_defect(const Layout &L, const float *u, const float *b, const float *
                   const float *diag, const float *W, const float *ib, float *rho, float *delta,
                   double *partials, cudaStream_t st)
 {
-    const int N = kVecF32;
-    const long long items = 2LL * ((L.P + 32 * N - 1) / (32 * N)) * L.njb * L.n3 * L.n4;
+    const int nch = (L.P + 32 * kVecF32 - 1) / (32 * kVecF32);
+    const long long items = item_count(L, nch);
     const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
-    k_defect<kVecF32><<<blocks, 256, 0, st>>>(L, u, b, gamma, diag, W, ib, rho, delta, partials);
+    k_defect<kVecF32><<<blocks, 256, 0, st>>>(L, u, b, gamma, diag, W, ib, rho, delta, partials,
+                                              make_item_decode(L, nch), (unsigned)items);
     return blocks;
 }
 

@@ -307,23 +307,13 @@ template <int N>
 __global__ void __launch_bounds__(256, 3) k_residual_vec(
     Layout L, const float *__restrict__ x, const float *__restrict__ beta,
     const float *__restrict__ gamma, const float *__restrict__ diag, const float *__restrict__ W,
-    double *__restrict__ partials)
+    double *__restrict__ partials, ItemDecode dec, unsigned items)
 {
-    const int nch = (L.P + 32 * N - 1) / (32 * N);
-    const long long items = 2LL * nch * L.njb * L.n3 * L.n4;
     Rec3f a = rec3f_init();
-    for (long long t = blockIdx.x; t < items; t += gridDim.x) {
-        const int C = (int)(t & 1);
-        long long r = t >> 1;
-        const int chunk = (int)(r % nch);
-        r /= nch;
-        const int jb = (int)(r % L.njb);
-        r /= L.njb;
+    for (unsigned t = blockIdx.x; t < items; t += gridDim.x) {
+        int C, chunk;
         RowPos rp;
-        rp.k = (int)(r % L.n3);
-        rp.l = (int)(r / L.n3);
-        rp.j = jb * 8 + (int)(threadIdx.x >> 5);
-        rp.p = (rp.j + rp.k + rp.l) & 1;
+        decode_item(dec, L, t, (int)(threadIdx.x >> 5), C, chunk, rp);
         const int s0 = chunk * 32 * N + N * (int)(threadIdx.x & 31);
         // whole warps leave together (rows past n2); lanes past the row end stay
         // for the shuffles of gather_vec
@@ -356,10 +346,11 @@ __global__ void __launch_bounds__(256, 3) k_residual_vec(
 int launch_residual(const Layout &L, const float *x, const float *beta, const float *gamma,
                     const float *diag, const float *W, double *partials, cudaStream_t st)
 {
-    const int N = kVecF32;
-    const long long items = 2LL * ((L.P + 32 * N - 1) / (32 * N)) * L.njb * L.n3 * L.n4;
+    const int nch = (L.P + 32 * kVecF32 - 1) / (32 * kVecF32);
+    const long long items = item_count(L, nch);
     const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
-    k_residual_vec<kVecF32><<<blocks, 256, 0, st>>>(L, x, beta, gamma, diag, W, partials);
+    k_residual_vec<kVecF32><<<blocks, 256, 0, st>>>(L, x, beta, gamma, diag, W, partials,
+                                                     make_item_decode(L, nch), (unsigned)items);
     return blocks;
 }
 
@@ -389,23 +380,15 @@ __global__ void __launch_bounds__(256, 2) k_step_coef(Layout L, const float *__r
                                                       float *__restrict__ gamma,
                                                       float *__restrict__ diag,
                                                       float *__restrict__ W,
-                                                      double *__restrict__ partials)
+                                                      double *__restrict__ partials,
+                                                      ItemDecode dec, unsigned items)
 {
-    const long long items = 2LL * L.nchunk * L.njb * L.n3 * L.n4;
     Rec3f a = rec3f_init();
-    for (long long t = blockIdx.x; t < items; t += gridDim.x) {
-        const int C = (int)(t & 1);
-        long long r = t >> 1;
-        const int chunk = (int)(r % L.nchunk);
-        r /= L.nchunk;
-        const int jb = (int)(r % L.njb);
-        r /= L.njb;
+    for (unsigned t = blockIdx.x; t < items; t += gridDim.x) {
+        int C, chunk;
         RowPos rp;
-        rp.k = (int)(r % L.n3);
-        rp.l = (int)(r / L.n3);
-        rp.j = jb * 8 + (int)(threadIdx.x >> 5);
+        decode_item(dec, L, t, (int)(threadIdx.x >> 5), C, chunk, rp);
         if (rp.j >= L.n2) continue;   // the whole warp
-        rp.p = (rp.j + rp.k + rp.l) & 1;
         const int s = chunk * 32 + (int)(threadIdx.x & 31);
         const bool act = s < L.P && 2 * s + (C ^ rp.p) < L.n1;
         const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
@@ -444,9 +427,10 @@ int launch_step_coef(const Layout &L, const float *u, const float *G, const doub
     }
     K.tau = (float)tau;
     K.eps2 = (float)(eps * eps);
-    const long long items = 2LL * L.nchunk * L.njb * L.n3 * L.n4;
+    const long long items = item_count(L, L.nchunk);
     const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
-    k_step_coef<<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials);
+    k_step_coef<<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials,
+                                        make_item_decode(L, L.nchunk), (unsigned)items);
     return blocks;
 }
 

@@ -62,6 +62,62 @@ struct RowPos {
     int j, k, l, p;
 };
 
+// Division of n < 2^31 by a runtime constant d >= 1 with a multiply-high and a
+// shift (round-up method): s = ceil(log2 d), m = ceil(2^(32+s) / d) - 2^32,
+// then n / d = (umulhi(n, m) + n) >> s; the sum stays below 2^32.
+struct FastDiv {
+    unsigned m, s, d, pad;
+};
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    unsigned s = 0;
+    while ((1ull << s) < d) ++s;
+    const unsigned long long m = ((1ull << (32 + s)) + d - 1) / d - (1ull << 32);
+    return FastDiv{(unsigned)m, s, d, 0};
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f)
+{
+    return (__umulhi(n, f.m) + n) >> f.s;
+}
+
+// Work items t = 2 * tile + colour of the tile loops: tile = (chunk, y-block
+// of 8 rows, k, l), chunk fastest, with nch chunks per row; the number of
+// items is below 2^31 (checked when the handle is created).
+struct ItemDecode {
+    FastDiv fch, fjb, fn3;
+    unsigned nch;
+};
+
+inline ItemDecode make_item_decode(const Layout &L, int nch)
+{
+    return ItemDecode{make_fastdiv((unsigned)nch), make_fastdiv((unsigned)L.njb),
+                      make_fastdiv((unsigned)L.n3), (unsigned)nch};
+}
+
+inline long long item_count(const Layout &L, int nch)
+{
+    return 2LL * nch * L.njb * L.n3 * L.n4;
+}
+
+// item t -> colour, chunk and the row position of warp `warp` (rp.p set)
+__device__ __forceinline__ void decode_item(const ItemDecode &D, const Layout &L, unsigned t,
+                                            int warp, int &C, int &chunk, RowPos &rp)
+{
+    C = (int)(t & 1u);
+    const unsigned r = t >> 1;
+    const unsigned a = fdiv(r, D.fch);
+    chunk = (int)(r - a * D.nch);
+    const unsigned b = fdiv(a, D.fjb);
+    const int jb = (int)(a - b * (unsigned)L.njb);
+    const unsigned c = fdiv(b, D.fn3);
+    rp.k = (int)(b - c * (unsigned)L.n3);
+    rp.l = (int)c;
+    rp.j = jb * 8 + warp;
+    rp.p = (rp.j + rp.k + rp.l) & 1;
+}
+
 // Sum over the 8 faces of  w_f * x_nb(f)  for the voxel in slot s of row `row`
 // (colour C, row parity p); neighbours outside the grid are Dirichlet zeros.
 // Red voxels own their 8 face weights; a black voxel reads each weight from
@@ -560,6 +616,10 @@ __device__ __forceinline__ void coef_gather(const Layout &L, const float *__rest
 // its 8 face edge coefficients g: A_f = sqrt(eps^2 + |grad^f u|^2),
 // Abar = sqrt(eps^2 + (1/8) sum_f |grad^f u|^2), w_f = G_f / (A_f h_d^2),
 // c = tau Abar, D = 1 + c sum_f w_f, beta = b / D, gamma = c / D (b = u0).
+// 1/A_f comes from rsqrtf (within 2 ulp) and both quotients by D from one
+// correctly rounded reciprocal: the coefficients are defined to FP32 accuracy,
+// not to the bit, and the solve meets its tolerance on whatever system they
+// form.
 __device__ __forceinline__ void coef_finish(const StepConst &K, const float (&g)[8], float u0,
                                             const float (&sm)[4], const float (&sp)[4],
                                             const float (&ed)[6][2][2], float (&w)[8],
@@ -575,13 +635,13 @@ __device__ __forceinline__ void coef_finish(const StepConst &K, const float (&g)
     float wsum = 0.0f;
 #pragma unroll
     for (int f = 0; f < 8; ++f) {
-        const float Af = sqrtf(K.eps2 + g2[f]);
-        w[f] = g[f] / Af * K.inv_h2[f >> 1];
+        w[f] = g[f] * rsqrtf(K.eps2 + g2[f]) * K.inv_h2[f >> 1];
         wsum += w[f];
     }
     D = 1.0f + cc * wsum;
-    bt = u0 / D;
-    gm = cc / D;
+    const float iD = __frcp_rn(D);
+    bt = u0 * iD;
+    gm = cc * iD;
 }
 
 // Sum over the interior faces of (w_f - bf16(w_f)) for the voxel in slot s
