@@ -47,6 +47,23 @@ def _env_int(name, default):
         return default
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of every rank's x (timed regions end with the slowest rank);
+    x itself when the job runs on one process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput of independent replicas: all ranks' units over the
+    slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -446,12 +463,8 @@ def main():
     e1.record(stream)
     barrier()
     clocks = sampler.stop()
-    elapsed_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * nvox * sweeps / (elapsed_ms / 1000.0)
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    value = job_rate(world, nvox * sweeps, elapsed_ms / 1000.0)
 
     # end to end through the same ABI with host buffers and copies in the timed region
     img_h = np.ascontiguousarray(case.image)
@@ -467,12 +480,8 @@ def main():
         e2e_sweeps += info["sweeps_total"]
         seg.read_u(out_h)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * nvox * e2e_sweeps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = job_rate(world, nvox * e2e_sweeps, e2e_s)
 
     # roofline of the dominant kernel (the sweep): algorithmic bytes of the
     # sweeps one launch performs / the launch's CUDA-event time

@@ -68,6 +68,7 @@ struct seg4d {
     bool need_u0 = false;
     bool has_u = false;
     bool has_coef = false;
+    bool scaled = false;   // beta/gamma/diag/W hold the symmetrically scaled system
     std::string err;
 };
 
@@ -216,12 +217,11 @@ struct SolveOut {
 // With `mixed` (precision 1) every check is a defect pass (exact residual,
 // right-hand side of the BF16 correction system, delta = 0), the sweeps run
 // on A_b delta = r with BF16 weights and u += delta follows each batch.
-seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol, int max_iters,
-                          int check_every, SolveOut &out, bool mixed = false)
+seg4d_status solve_loop(seg4d *h, float *x, const float *gam, double omega, double tol,
+                        int max_iters, int check_every, SolveOut &out, bool mixed)
 {
     const Layout &L = h->L;
-    seg4d_status st = reduce_into(h, 0, brec);   // scal[0..2] = sum b^2, min b, max b
-    if (st) return st;
+    seg4d_status st = SEG4D_OK;
     int it = 0;
     bool timed_batch = false;
     // Checks are spaced by a prediction from the observed contraction: after
@@ -245,8 +245,7 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
             nrec = launch_defect(L, x, h->beta, h->gamma, h->diag, h->W, h->ib, h->rho, h->dlt,
                                  h->partials, h->stream);
         else
-            nrec = launch_residual(L, x, h->beta, h->gamma, h->diag, h->W, h->partials,
-                                   h->stream);
+            nrec = launch_residual(L, x, h->beta, gam, h->diag, h->W, h->partials, h->stream);
         h->launches += 1;
         CK_LAUNCH("residual");
         if ((st = reduce_into(h, 3, nrec))) return st;   // scal[3..5] = sum r^2, min u, max u
@@ -303,15 +302,15 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
         } else if (h->p.sweep_variant == 0) {
             CK(cudaMemsetAsync(h->wave_ctrl, 0, (4 + h->wave_T) * sizeof(unsigned), h->stream));
             const int per_sm = std::min(h->p.ctas_per_sm > 0 ? h->p.ctas_per_sm : 4, h->wave_occ);
-            launch_sweep_wave(L, n, x, h->beta, h->gamma, h->W, (float)omega, h->wave_ctrl,
+            launch_sweep_wave(L, n, x, h->beta, gam, h->W, (float)omega, h->wave_ctrl,
                               per_sm * h->num_sms, h->p.wait_test, h->stream);
             h->launches += 1;
             h->sweep_launches += 1;
             CK_LAUNCH("sweep_wave");
         } else {
             for (int s = 0; s < n; ++s) {
-                launch_sweep(L, 0, x, h->beta, h->gamma, h->W, (float)omega, h->stream);
-                launch_sweep(L, 1, x, h->beta, h->gamma, h->W, (float)omega, h->stream);
+                launch_sweep(L, 0, x, h->beta, gam, h->W, (float)omega, h->stream);
+                launch_sweep(L, 1, x, h->beta, gam, h->W, (float)omega, h->stream);
             }
             h->launches += 2LL * n;
             h->sweep_launches += 2LL * n;
@@ -327,6 +326,49 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
             wave_pending = true;
         }
     }
+}
+
+// The solve of the system in beta/gamma/diag/W for x, with the ||b|| records
+// (brec of them) in `partials`.  Plain FP32 solves run on the symmetrically
+// scaled system (launch_scale_system: the sweeps read no gamma) and map x
+// back to u at the end; the arrays stay scaled until the next coefficient
+// kernel (read_field maps them back on demand).  Mixed solves run on the
+// original system.
+seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol, int max_iters,
+                          int check_every, SolveOut &out, bool mixed = false)
+{
+    seg4d_status st = reduce_into(h, 0, brec);   // scal[0..2] = sum b^2, min b, max b
+    if (st) return st;
+    h->scaled = false;
+    if (!mixed) {
+        launch_scale_system(h->L, x, h->beta, h->gamma, h->diag, h->W, false, h->stream);
+        h->launches += 2;
+        CK_LAUNCH("scale_system");
+        h->scaled = true;
+    }
+    st = solve_loop(h, x, mixed ? h->gamma : nullptr, omega, tol, max_iters, check_every, out,
+                    mixed);
+    if (!mixed && (st == SEG4D_OK || st == SEG4D_ERR_NOT_CONVERGED)) {
+        const int nrec = launch_unscale(h->L, x, h->gamma, h->partials, h->stream);
+        h->launches += 1;
+        CK_LAUNCH("unscale");
+        seg4d_status s2 = reduce_into(h, 3, nrec);   // scal[3..5] = sum u^2, min u, max u
+        if (!s2) s2 = fetch_scal(h);
+        if (s2) return s2;
+        out.umin = h->host_scal[4];
+        out.umax = h->host_scal[5];
+    }
+    return st;
+}
+
+// the step coefficients in beta/gamma/diag/W in their original form
+seg4d_status unscale_coefficients(seg4d *h)
+{
+    if (!h->scaled) return SEG4D_OK;
+    launch_scale_system(h->L, nullptr, h->beta, h->gamma, h->diag, h->W, true, h->stream);
+    CK_LAUNCH("scale_system");
+    h->scaled = false;
+    return SEG4D_OK;
 }
 
 seg4d_status upload_seeds(seg4d *h)
@@ -868,6 +910,7 @@ seg4d_status seg4d_read_field(seg4d *h, int field, float *dst, size_t n, int on_
     case SEG4D_FIELD_DIAG:
     case SEG4D_FIELD_OFF:
         if (!h->has_coef) return fail(h, SEG4D_ERR_STATE, "no step coefficients computed");
+        if ((st = unscale_coefficients(h))) return st;
         break;
     default:
         return fail(h, SEG4D_ERR_INVALID, "unknown field");

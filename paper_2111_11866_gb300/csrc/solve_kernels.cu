@@ -44,7 +44,7 @@ namespace seg4d_impl {
 // black pass walks the grid backwards, so it starts on the data the red pass
 // touched last, which is still in L2.  The same kernel with BF16 weights
 // sweeps the correction system of the mixed-precision solve.
-template <int C, typename WT, int N>
+template <int C, typename WT, int N, bool kUnit>
 __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_sweep_vec(
     Layout L, float *__restrict__ x, const float *__restrict__ B, const float *__restrict__ Gm,
     const WT *__restrict__ W, float omega)
@@ -62,10 +62,10 @@ __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_sweep_vec(
     const int s0 = chunk * 32 * N + N * threadIdx.x;
     const bool act = s0 < L.P && 2 * s0 + (C ^ rp.p) < L.n1;
     const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
-    relax_vec<C, WT, N>(L, x, B, Gm, W, omega, act, row, s0, rp);
+    relax_vec<C, WT, N, kUnit>(L, x, B, Gm, W, omega, act, row, s0, rp);
 }
 
-template <typename WT, int N>
+template <typename WT, int N, bool kUnit>
 void launch_vec(const Layout &L, int colour, float *x, const float *B, const float *Gm,
                 const WT *W, float omega, cudaStream_t st)
 {
@@ -73,22 +73,25 @@ void launch_vec(const Layout &L, int colour, float *x, const float *B, const flo
     dim3 grid((unsigned)(((L.P + 32 * N - 1) / (32 * N)) * L.njb), (unsigned)L.n3,
               (unsigned)L.n4);
     if (colour == 0)
-        k_sweep_vec<0, WT, N><<<grid, block, 0, st>>>(L, x, B, Gm, W, omega);
+        k_sweep_vec<0, WT, N, kUnit><<<grid, block, 0, st>>>(L, x, B, Gm, W, omega);
     else
-        k_sweep_vec<1, WT, N><<<grid, block, 0, st>>>(L, x, B, Gm, W, omega);
+        k_sweep_vec<1, WT, N, kUnit><<<grid, block, 0, st>>>(L, x, B, Gm, W, omega);
 }
 
 void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,
                   const float *W, float omega, cudaStream_t st)
 {
-    launch_vec<float, kVecF32>(L, colour, x, beta, gamma, W, omega, st);
+    if (gamma)
+        launch_vec<float, kVecF32, false>(L, colour, x, beta, gamma, W, omega, st);
+    else
+        launch_vec<float, kVecF32, true>(L, colour, x, beta, nullptr, W, omega, st);
 }
 
 void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *rho,
                         const float *gb, const void *Wb, float omega, cudaStream_t st)
 {
-    launch_vec<__nv_bfloat16, kVecBF16>(L, colour, delta, rho, gb, (const __nv_bfloat16 *)Wb,
-                                        omega, st);
+    launch_vec<__nv_bfloat16, kVecBF16, false>(L, colour, delta, rho, gb,
+                                               (const __nv_bfloat16 *)Wb, omega, st);
 }
 
 // ------------------------------------------ fused red-black wavefront sweep
@@ -201,7 +204,8 @@ __device__ __forceinline__ void wave_rows(const Layout &L, float *__restrict__ x
                 if (rp.j < L.n2 && s < L.P && 2 * s + (C ^ rp.p) < L.n1) {
                     const long long q = rb + s;
                     const float acc = neighbour_sum<C, true>(L, xo, W, row, s, rp);
-                    val[r][m] = relax(__ldcg(xs + q), beta[C * L.S + q], gamma[C * L.S + q],
+                    val[r][m] = relax(__ldcg(xs + q), beta[C * L.S + q],
+                                      gamma ? gamma[C * L.S + q] : 1.0f,
                                       acc, omega);
                 }
             }
@@ -303,7 +307,7 @@ void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta
 // sweep's Gauss-Seidel value; records (sum r^2, min u, max u) per block.
 // Work item t = 2 * tile + colour, tile = one block of the sweep grid
 // (32 N slots x 8 rows at one (k, l)); blocks stride over the items.
-template <int N>
+template <int N, bool kUnit>
 __global__ void __launch_bounds__(256, 3) k_residual_vec(
     Layout L, const float *__restrict__ x, const float *__restrict__ beta,
     const float *__restrict__ gamma, const float *__restrict__ diag, const float *__restrict__ W,
@@ -324,7 +328,12 @@ __global__ void __launch_bounds__(256, 3) k_residual_vec(
         float Xs[N], Bp[N], Gp[N], Dp[N], acc[N];
         ldv<N>(Xs, act, x + q);
         ldv<N>(Bp, act, beta + q);
-        ldv<N>(Gp, act, gamma + q);
+        if (kUnit) {
+#pragma unroll
+            for (int m = 0; m < N; ++m) Gp[m] = 1.0f;
+        } else {
+            ldv<N>(Gp, act, gamma + q);
+        }
         ldv<N>(Dp, act, diag + q);
         if (C)
             gather_vec<1, float, N>(L, x, W, act, row, s0, rp, acc);
@@ -349,8 +358,144 @@ int launch_residual(const Layout &L, const float *x, const float *beta, const fl
     const int nch = (L.P + 32 * kVecF32 - 1) / (32 * kVecF32);
     const long long items = item_count(L, nch);
     const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
-    k_residual_vec<kVecF32><<<blocks, 256, 0, st>>>(L, x, beta, gamma, diag, W, partials,
-                                                     make_item_decode(L, nch), (unsigned)items);
+    if (gamma)
+        k_residual_vec<kVecF32, false><<<blocks, 256, 0, st>>>(
+            L, x, beta, gamma, diag, W, partials, make_item_decode(L, nch), (unsigned)items);
+    else
+        k_residual_vec<kVecF32, true><<<blocks, 256, 0, st>>>(
+            L, x, beta, nullptr, diag, W, partials, make_item_decode(L, nch), (unsigned)items);
+    return blocks;
+}
+
+// ---------------------------------------------------- symmetric scaling
+
+// The step (or presmoothing) system D u - c sum_f w_f u_nb = b, divided by
+// c row by row, is M u = b / c with the symmetric M = diag(D/c) - W.  With
+// s = sqrt(D/c) = 1/sqrt(gamma) and v = s u it becomes (I - Wt) v = bt,
+//   Wt_f = w_f r_i r_nb(f),  bt = beta / r,  r = sqrt(gamma) = 1/s,
+// whose Gauss-Seidel / SOR iterates are those of the original system mapped
+// by v = u / r (row and variable scaling by positive diagonals).  A sweep
+// then reads bt and Wt and no gamma: one stream fewer per voxel-sweep.  The
+// residual of the original system is b - A u = (D r) (bt + sum_f Wt_f v_nb -
+// v), so diag holds D r.  `inverse` maps the arrays back.
+//
+// Face weights (red ends): w <-> w r_i r_nb on the interior faces of every red
+// voxel; r of both ends from gamma (sqrt of it, or gamma itself if inverse).
+__global__ void __launch_bounds__(256) k_scale_weights(Layout L, float *__restrict__ W,
+                                                       const float *__restrict__ gamma,
+                                                       bool inverse, ItemDecode dec,
+                                                       unsigned items)
+{
+    for (unsigned t = blockIdx.x; t < items; t += gridDim.x) {
+        int C, chunk;
+        RowPos rp;
+        decode_item(dec, L, 2u * t, (int)(threadIdx.x >> 5), C, chunk, rp);   // red tiles
+        if (rp.j >= L.n2) continue;
+        const int s = chunk * 32 + (int)(threadIdx.x & 31);
+        if (s >= L.P || 2 * s + rp.p >= L.n1) continue;
+        const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
+        const long long q = (long long)row * L.P + s;
+        const long long dy = L.P, dz = (long long)L.n2 * L.P, dt = (long long)L.n2 * L.n3 * L.P;
+        const float *gb = gamma + L.S;   // black neighbours
+        const int i = 2 * s + rp.p;
+        const long long nb[8] = {q - 1 + rp.p, q + rp.p, q - dy, q + dy, q - dz, q + dz,
+                                 q - dt, q + dt};
+        const bool in[8] = {i >= 1, i + 1 < L.n1, rp.j > 0, rp.j + 1 < L.n2,
+                            rp.k > 0, rp.k + 1 < L.n3, rp.l > 0, rp.l + 1 < L.n4};
+        const float gs = gamma[q];
+        const float rs = inverse ? gs : sqrtf(gs);
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+            if (!in[f]) continue;
+            const float gn = gb[nb[f]];
+            const float rn = inverse ? gn : sqrtf(gn);
+            float *w = W + (long long)f * L.S + q;
+            *w = inverse ? *w / (rs * rn) : *w * rs * rn;
+        }
+    }
+}
+
+// Per voxel: beta <-> beta / r, diag <-> D r, gamma <-> r, and (when x is
+// given) x <-> x / r, over both colours; padding slots (gamma = 0) untouched.
+__global__ void __launch_bounds__(256) k_scale_fields(long long n4, float4 *__restrict__ beta,
+                                                      float4 *__restrict__ gamma,
+                                                      float4 *__restrict__ diag,
+                                                      float4 *__restrict__ x, bool inverse)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n4;
+         e += (long long)gridDim.x * blockDim.x) {
+        float4 b = beta[e], g = gamma[e], d = diag[e], v = x ? x[e] : make_float4(0, 0, 0, 0);
+        float *bp = &b.x, *gp = &g.x, *dp = &d.x, *vp = &v.x;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if (!(gp[m] > 0.0f)) continue;
+            const float r = inverse ? gp[m] : sqrtf(gp[m]);
+            bp[m] = inverse ? bp[m] * r : bp[m] / r;
+            dp[m] = inverse ? dp[m] / r : dp[m] * r;
+            gp[m] = inverse ? r * r : r;
+            vp[m] = inverse ? vp[m] * r : vp[m] / r;
+        }
+        beta[e] = b;
+        gamma[e] = g;
+        diag[e] = d;
+        if (x) x[e] = v;
+    }
+}
+
+// x <- x r (back to u) with records (sum x^2, min x, max x) of the result
+__global__ void __launch_bounds__(kPartThreads) k_unscale(long long n4, float4 *__restrict__ x,
+                                                          const float4 *__restrict__ r,
+                                                          double *__restrict__ partials)
+{
+    Rec3f a = rec3f_init();
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n4;
+         e += (long long)gridDim.x * blockDim.x) {
+        float4 v = x[e];
+        const float4 g = r[e];
+        float *vp = &v.x;
+        const float *gp = &g.x;
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (gp[m] > 0.0f) {
+                vp[m] = vp[m] * gp[m];
+                rec3f_add(a, __fmul_rn(vp[m], vp[m]), vp[m]);
+            }
+        x[e] = v;
+    }
+    block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
+}
+
+static int elem_blocks(long long n4)
+{
+    long long b = (n4 + 255) / 256;
+    if (b > kPartBlocks) b = kPartBlocks;
+    return (int)(b < 1 ? 1 : b);
+}
+
+void launch_scale_system(const Layout &L, float *x, float *beta, float *gamma, float *diag,
+                         float *W, bool inverse, cudaStream_t st)
+{
+    const long long red_items = item_count(L, L.nchunk) / 2;
+    const int blocks = (int)(red_items < kResBlocks ? red_items : kResBlocks);
+    const long long n4 = 2 * L.S / 4;   // P is a multiple of 4
+    if (inverse) {   // weights first: they need r before gamma goes back to r^2
+        k_scale_weights<<<blocks, 256, 0, st>>>(L, W, gamma, true, make_item_decode(L, L.nchunk),
+                                                (unsigned)red_items);
+        k_scale_fields<<<elem_blocks(n4), 256, 0, st>>>(n4, (float4 *)beta, (float4 *)gamma,
+                                                        (float4 *)diag, (float4 *)x, true);
+    } else {
+        k_scale_weights<<<blocks, 256, 0, st>>>(L, W, gamma, false,
+                                                make_item_decode(L, L.nchunk), (unsigned)red_items);
+        k_scale_fields<<<elem_blocks(n4), 256, 0, st>>>(n4, (float4 *)beta, (float4 *)gamma,
+                                                        (float4 *)diag, (float4 *)x, false);
+    }
+}
+
+int launch_unscale(const Layout &L, float *x, const float *r, double *partials, cudaStream_t st)
+{
+    const long long n4 = 2 * L.S / 4;
+    const int blocks = elem_blocks(n4);
+    k_unscale<<<blocks, kPartThreads, 0, st>>>(n4, (float4 *)x, (const float4 *)r, partials);
     return blocks;
 }
 

@@ -413,9 +413,10 @@ __device__ __forceinline__ void flux_residual_vec(const Layout &L, const float *
 
 // One colour-C relaxation of the N voxels of a group (see gather_vec):
 // x <- x + omega (B + G acc - x) with B and G the [2][S] per-voxel
-// coefficients, the arithmetic of neighbour_sum + relax.  Slots past the row
-// end (i >= n1) are padding and keep their value (zero).
-template <int C, typename WT, int N>
+// coefficients, the arithmetic of neighbour_sum + relax.  kUnit: G = 1 (the
+// symmetrically scaled system, where no G is stored or read).  Slots past the
+// row end (i >= n1) are padding and keep their value (zero).
+template <int C, typename WT, int N, bool kUnit = false>
 __device__ __forceinline__ void relax_vec(const Layout &L, float *__restrict__ x,
                                           const float *__restrict__ B,
                                           const float *__restrict__ Gm,
@@ -428,7 +429,12 @@ __device__ __forceinline__ void relax_vec(const Layout &L, float *__restrict__ x
     float Xs[N], Bp[N], Gp[N], acc[N];
     ldv<N>(Xs, act, xs + q);
     ldv<N>(Bp, act, B + C * S + q);
-    ldv<N>(Gp, act, Gm + C * S + q);
+    if (kUnit) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) Gp[m] = 1.0f;
+    } else {
+        ldv<N>(Gp, act, Gm + C * S + q);
+    }
     gather_vec<C, WT, N>(L, x, W, act, row, s0, rp, acc);
     if (!act) return;
     const int e = C ^ rp.p;
@@ -616,10 +622,10 @@ __device__ __forceinline__ void coef_gather(const Layout &L, const float *__rest
 // its 8 face edge coefficients g: A_f = sqrt(eps^2 + |grad^f u|^2),
 // Abar = sqrt(eps^2 + (1/8) sum_f |grad^f u|^2), w_f = G_f / (A_f h_d^2),
 // c = tau Abar, D = 1 + c sum_f w_f, beta = b / D, gamma = c / D (b = u0).
-// 1/A_f comes from rsqrtf (within 2 ulp) and both quotients by D from one
-// correctly rounded reciprocal: the coefficients are defined to FP32 accuracy,
-// not to the bit, and the solve meets its tolerance on whatever system they
-// form.
+// 1/A_f is a correctly rounded reciprocal square root and both quotients by
+// D use one correctly rounded reciprocal (IEEE operations, no approximate
+// intrinsics): the coefficients are defined to FP32 accuracy, not to the bit,
+// and the solve meets its tolerance on whatever system they form.
 __device__ __forceinline__ void coef_finish(const StepConst &K, const float (&g)[8], float u0,
                                             const float (&sm)[4], const float (&sp)[4],
                                             const float (&ed)[6][2][2], float (&w)[8],
@@ -635,7 +641,7 @@ __device__ __forceinline__ void coef_finish(const StepConst &K, const float (&g)
     float wsum = 0.0f;
 #pragma unroll
     for (int f = 0; f < 8; ++f) {
-        w[f] = g[f] * rsqrtf(K.eps2 + g2[f]) * K.inv_h2[f >> 1];
+        w[f] = g[f] * __frsqrt_rn(K.eps2 + g2[f]) * K.inv_h2[f >> 1];
         wsum += w[f];
     }
     D = 1.0f + cc * wsum;
