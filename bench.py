@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 # it is captured again.
 SWEEP_KERNELS = {0: "k_sweep_wave (fused red-black wavefront, several sweeps per launch)",
                  1: "k_sweep_vec (one colour of a red-black sweep per launch, 2 voxels/thread)"}
-SWEEP_TRAFFIC_PER_SWEEP = {0: None, 1: None}
+SWEEP_TRAFFIC_PER_SWEEP = {0: None, 1: 793.4e6 + 791.5e6}
 
 
 def _env_int(name, default):

@@ -17,6 +17,20 @@
 using namespace seg4d_impl;
 
 namespace seg4d_impl {
+int next_check_batch(double rn, double prev_rn, int it, int prev_it, double tol, double bnorm,
+                     int check_every, bool mixed)
+{
+    if (!(prev_rn > 0.0 && rn < prev_rn && it > prev_it && rn > 0.0)) return check_every;
+    const double gain = mixed ? 1e-2 : 1e-3;
+    const double rho = std::pow(rn / prev_rn, 1.0 / (it - prev_it));
+    const double need = std::log(tol * bnorm / rn) / std::log(rho);
+    const double cap = std::log(gain) / std::log(rho);
+    const int lo = std::max(1, check_every / 4), hi = 8 * check_every;
+    const double want = std::ceil(std::min(0.8 * need, cap));
+    return std::isfinite(want) ? (int)std::min<double>(hi, std::max<double>(lo, want))
+                               : check_every;
+}
+
 // message of the last failed handle-free call of this thread (seg4d_create,
 // seg4d_residual_norms_noalloc), reported by seg4d_last_error(NULL)
 std::string &handle_free_error()
@@ -224,17 +238,7 @@ seg4d_status solve_loop(seg4d *h, float *x, const float *gam, double omega, doub
     seg4d_status st = SEG4D_OK;
     int it = 0;
     bool timed_batch = false;
-    // Checks are spaced by a prediction from the observed contraction: after
-    // two checks with r_now < r_prev, rho = (r_now/r_prev)^(1/sweeps) and
-    // need = log(tol*||b|| / r_now) / log(rho) sweeps remain.  SOR contracts
-    // faster as it proceeds, so need over-estimates: the next batch is
-    // 0.8 * need, and at most the sweeps that cut the residual by the factor
-    // `gain` at rate rho, so that rho is re-measured on the way.  A mixed
-    // cycle cannot gain much more than the inverse of the BF16 weight error
-    // (about 2^9) before the correction system's own error dominates, so
-    // mixed cycles aim at 1e-2, plain batches at 1e-3.  Batches are kept in
-    // [max(1, check_every/4), 8*check_every]; the first is check_every.
-    const double gain = mixed ? 1e-2 : 1e-3;
+    // checks spaced by next_check_batch (seg4d_internal.cuh)
     int batch = check_every;
     double prev_rn = -1.0;
     int prev_it = 0;
@@ -275,17 +279,7 @@ seg4d_status solve_loop(seg4d *h, float *x, const float *gam, double omega, doub
             return SEG4D_OK;
         }
         if (it >= max_iters) return SEG4D_OK;   // not converged; caller reports it
-        if (prev_rn > 0.0 && rn < prev_rn && it > prev_it && rn > 0.0) {
-            const double rho = std::pow(rn / prev_rn, 1.0 / (it - prev_it));
-            const double need = std::log(tol * bn / rn) / std::log(rho);
-            const double cap = std::log(gain) / std::log(rho);
-            const int lo = std::max(1, check_every / 4), hi = 8 * check_every;
-            const double want = std::ceil(std::min(0.8 * need, cap));
-            batch = std::isfinite(want) ? (int)std::min<double>(hi, std::max<double>(lo, want))
-                                        : check_every;
-        } else {
-            batch = check_every;
-        }
+        batch = next_check_batch(rn, prev_rn, it, prev_it, tol, bn, check_every, mixed);
         prev_rn = rn;
         prev_it = it;
         const int n = std::min(batch, max_iters - it);

@@ -770,24 +770,44 @@ struct SolveItem {
     int iters;
     bool done;
     bool ok;
+    int next_check;     // sweep count of the window's next stopping test
+    double prev_rn;     // residual norm at its previous test (-1: none yet)
+    int prev_it;
 };
 
 // Batched red-black SOR over every window of `items` (each window's d.x,
 // beta, gamma, diag, W already set up).  Per window: stop when
-// ||b - A x|| <= tol ||b||, tested every check_every sweeps.
+// ||b - A x|| <= tol ||b||.  Each window has its own check schedule
+// (next_check_batch on its own residual history): every round sweeps all
+// active windows up to the earliest pending check, then tests the windows
+// whose check is due (in mixed precision: u += delta, then the defect pass
+// for those only).  A window's sweeps and tests therefore do not depend on
+// the other windows, and its result is the same alone or in any mix.
 seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double omega, double tol,
                          int max_iters, int check_every, long long &sweeps_total,
                          bool mixed = false)
 {
-    std::vector<SolveItem *> act;
-    for (auto &it : items) act.push_back(&it);
+    std::vector<SolveItem *> act, due;
+    for (auto &it : items) {
+        it.next_check = 0;
+        it.prev_rn = -1.0;
+        it.prev_it = 0;
+        act.push_back(&it);
+    }
+    due = act;
     int it = 0;
     bool timed = false;
-    while (!act.empty()) {
+    seg4d_status st;
+    for (;;) {
+        // test the windows whose check is due at sweep `it`
         std::vector<Window *> ws;
-        for (auto *a : act) ws.push_back(a->w);
-        seg4d_status st;
+        for (auto *a : due) ws.push_back(a->w);
         if ((st = set_table(b, ws))) return st;
+        if (mixed && it > 0) {
+            k_bapply<<<(unsigned)b->n_tile, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
+                                                                 (int)ws.size());
+            b->launches += 1;
+        }
         const long long nch = b->n_chunk;
         if ((st = ensure_parts(b, nch))) return st;
         if (mixed)
@@ -804,39 +824,43 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
             if (cudaEventElapsedTime(&ms, b->e0, b->e1) == cudaSuccess) b->sweep_ms += ms;
             timed = false;
         }
-        std::vector<SolveItem *> next;
-        for (size_t i = 0; i < act.size(); ++i) {
-            SolveItem *a = act[i];
+        for (size_t i = 0; i < due.size(); ++i) {
+            SolveItem *a = due[i];
             const double rn = std::sqrt(b->h_out[3 * i]);
             a->w->last_res_rel = a->bnorm > 0 ? rn / a->bnorm : rn;
             if (!std::isfinite(rn)) {
                 a->done = true;
                 a->ok = false;
                 a->w->err = "residual is not finite";
-                continue;
-            }
-            if (rn <= tol * a->bnorm) {
+            } else if (rn <= tol * a->bnorm) {
                 a->done = true;
                 a->ok = true;
                 a->iters = it;
-                continue;
-            }
-            if (it >= max_iters) {
+            } else if (it >= max_iters) {
                 a->done = true;
                 a->ok = false;
                 a->iters = it;
                 a->w->err = "solve reached max_iters";
-                continue;
+            } else {
+                const int n = next_check_batch(rn, a->prev_rn, it, a->prev_it, tol, a->bnorm,
+                                               check_every, mixed);
+                a->prev_rn = rn;
+                a->prev_it = it;
+                a->next_check = std::min(it + n, max_iters);
             }
-            next.push_back(a);
         }
+        std::vector<SolveItem *> next;
+        for (auto *a : act)
+            if (!a->done) next.push_back(a);
         act.swap(next);
         if (act.empty()) break;
+        // sweep every active window up to the earliest pending check
+        int until = max_iters;
+        for (auto *a : act) until = std::min(until, a->next_check);
+        const int n = until - it;
         ws.clear();
         for (auto *a : act) ws.push_back(a->w);
         if ((st = set_table(b, ws))) return st;
-        const long long ntiles = b->n_tile;
-        const int n = std::min(check_every, max_iters - it);
         BCK(cudaEventRecord(b->e0, b->stream));
         const long long nptiles = b->n_ptile;
         const int nw = (int)ws.size();
@@ -853,17 +877,15 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
                     b->d_wins, b->d_ptile, nw, (float)omega);
             }
         }
-        if (mixed) {
-            k_bapply<<<(unsigned)ntiles, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
-                                                              (int)ws.size());
-            b->launches += 1;
-        }
         b->launches += 2LL * n;
         BCK(cudaGetLastError());
         BCK(cudaEventRecord(b->e1, b->stream));
         timed = true;
         sweeps_total += (long long)n * (long long)act.size();
-        it += n;
+        it = until;
+        due.clear();
+        for (auto *a : act)
+            if (a->next_check == it) due.push_back(a);
     }
     return SEG4D_OK;
 }
@@ -969,7 +991,7 @@ seg4d_status batch_setup(seg4d_batch *b, std::vector<Window *> &pend, long long 
         if ((st = reduce_windows(b, ws.size()))) return st;
         std::vector<SolveItem> items;
         for (size_t i = 0; i < ws.size(); ++i)
-            items.push_back(SolveItem{ws[i], std::sqrt(b->h_out[3 * i]), 0, false, false});
+            items.push_back(SolveItem{ws[i], std::sqrt(b->h_out[3 * i]), 0, false, false, 0, -1.0, 0});
         if ((st = batch_solve(b, items, p.omega_smooth, p.tol_smooth, p.max_iters, p.check_every,
                               sweeps)))
             return st;
@@ -1029,7 +1051,7 @@ seg4d_status batch_step(seg4d_batch *b, std::vector<Window *> &act, long long &s
     if ((st = reduce_windows(b, act.size()))) return st;
     std::vector<SolveItem> items;
     for (size_t i = 0; i < act.size(); ++i)
-        items.push_back(SolveItem{act[i], std::sqrt(b->h_out[3 * i]), 0, false, false});
+        items.push_back(SolveItem{act[i], std::sqrt(b->h_out[3 * i]), 0, false, false, 0, -1.0, 0});
     if ((st = batch_solve(b, items, p.omega, p.tol, p.max_iters, p.check_every, sweeps, mixed)))
         return st;
     std::vector<Window *> ok;

@@ -155,6 +155,20 @@ int launch_residual(const Layout &L, const float *x, const float *beta, const fl
                     const float *diag, const float *W, double *partials, cudaStream_t st);
 void launch_reduce_partials(const double *partials, int nparts, double *out, cudaStream_t st);
 
+// Sweeps until the next stopping test of a solve.  After two checks with
+// r_now < r_prev, rho = (r_now/r_prev)^(1/sweeps) and need = log(tol*||b|| /
+// r_now) / log(rho) sweeps remain.  SOR contracts faster as it proceeds, so
+// need over-estimates: the next batch is 0.8 * need, and at most the sweeps
+// that cut the residual by the factor `gain` at rate rho, so that rho is
+// re-measured on the way.  A mixed-precision cycle cannot gain much more than
+// the inverse of the BF16 weight error (about 2^9) before the correction
+// system's own error dominates, so mixed cycles aim at 1e-2, plain batches at
+// 1e-3.  Batches are kept in [max(1, check_every/4), 8*check_every]; without
+// two usable checks the batch is check_every.  The result depends only on the
+// solve's own residual history.
+int next_check_batch(double rn, double prev_rn, int it, int prev_it, double tol, double bnorm,
+                     int check_every, bool mixed);
+
 // message of the last failed handle-free call of this thread (api.cu)
 std::string &handle_free_error();
 

@@ -58,6 +58,30 @@ def tiny(seed: int = 1, n=(32, 32, 32, 16), radius: float = 8.0, speed: float = 
                 {"radius": radius, "speed": speed, "noise": noise, "gap_deg": gap_deg})
 
 
+def moving_sphere(seed: int = 6, n=(32, 32, 32, 20), radius: float = 6.0, speed: float = 0.5,
+                  noise: float = 0.05, missing=(5, 10, 15), nsteps: int = 10) -> Case:
+    """A sphere of radius `radius` (1 inside, 0 outside) moving `speed` voxels
+    per frame along x, with Gaussian noise, and the frames in `missing` blanked
+    (background only): the missing-frame experiment of Section 4.  Seeds at the
+    sphere centre of every frame (the path is known; only the image data of the
+    missing frames is absent)."""
+    rng = np.random.default_rng(seed)
+    n1, n2, n3, n4 = n
+    cx0, cy, cz = n1 / 2 - speed * (n4 - 1) / 2, float(n2 // 2), float(n3 // 2)
+    z, y, x = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    img = np.zeros((n4, n3, n2, n1), np.float32)
+    truth = np.zeros((n4, n3, n2, n1), bool)
+    for l in range(n4):
+        cx = cx0 + speed * l
+        truth[l] = (x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2 <= radius ** 2
+        if l not in missing:
+            img[l] = truth[l]
+    img += rng.normal(0.0, noise, size=img.shape).astype(np.float32)
+    seeds = np.array([[round(cx0 + speed * l), cy, cz, l] for l in range(n4)], dtype=np.float64)
+    return Case(f"moving sphere {n1}x{n2}x{n3}x{n4}, frames {tuple(missing)} missing", img, seeds,
+                nsteps, {"truth": truth, "missing": tuple(missing), "radius": radius})
+
+
 # --------------------------------------------------------------------------
 # nuclei: ellipsoids with Gaussian profiles on smooth trajectories
 # --------------------------------------------------------------------------

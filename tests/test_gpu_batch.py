@@ -74,8 +74,9 @@ def test_batch_result_same_alone_and_in_mix():
 
 
 def test_batch_matches_single_grid_path():
-    """Same scheme as seg4d_step, up to the check schedule of the stopping
-    rule (fixed spacing here, predicted spacing there)."""
+    """Same scheme as seg4d_step, up to rounding (the single grid solves the
+    symmetrically scaled form of the same system) and the stopping rule's
+    check schedule."""
     p = _params()
     img, seeds, nsteps = _window(*WINDOWS[0])
     res = _run_batch({0: (img, seeds, nsteps)}, p)

@@ -1,0 +1,65 @@
+"""Parity beyond the benchmark workloads: anisotropic grid spacing (Eq. new1
+with h_1..h_4) and the missing-frame experiment of Section 4 (a moving sphere
+whose image data is absent in some frames; the 4D segmentation still labels
+the sphere there)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2111_11866_gb300 import _lib, synth
+
+from gpu_common import REL_TOL, gpu_run, label_mismatch_outside_band, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2111_11866_gb300 import build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("h", [(0.01, 0.01, 0.025, 0.04), (0.02, 0.01, 0.01, 0.005)])
+def test_anisotropic_spacing_matches_oracle(h):
+    """Microscopy stacks have a coarser z spacing and a time axis of its own."""
+    c = synth.small_nuclei(seed=17, n=(41, 27, 15, 6), count=3, nsteps=3)
+    p = _lib.Params.defaults()
+    p.r_ball = p.R_init = 6.0
+    p.h = tuple(h)
+    gpu = gpu_run(c.image, c.seeds, c.nsteps, p)
+    ref, _ = O.segment(c.image.astype(np.float64), c.seeds, oracle_params(p), nsteps=c.nsteps)
+    err = np.abs(gpu["u"] - ref).max()
+    assert err <= REL_TOL * np.abs(ref).max(), err
+    assert label_mismatch_outside_band(gpu["u"], ref) == 0
+    assert gpu["info"]["res_rel"] <= p.tol
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    c = synth.moving_sphere(n=(24, 24, 24, 12), radius=5.0, missing=(3, 6, 9), nsteps=20)
+    p = _lib.Params.defaults()
+    p.r_ball = p.R_init = 6.0
+    gpu = gpu_run(c.image, c.seeds, c.nsteps, p)
+    ref, _ = O.segment(c.image.astype(np.float64), c.seeds, oracle_params(p), nsteps=c.nsteps)
+    return c, gpu, ref, p
+
+
+def test_missing_frames_match_oracle(sphere):
+    c, gpu, ref, p = sphere
+    err = np.abs(gpu["u"] - ref).max()
+    assert err <= REL_TOL * np.abs(ref).max(), err
+    assert label_mismatch_outside_band(gpu["u"], ref) == 0
+
+
+def test_missing_frames_are_filled(sphere):
+    """In the frames without image data the label still covers the sphere
+    (intersection over union with the true sphere)."""
+    c, gpu, _, _ = sphere
+    truth = c.meta["truth"]
+    for l in c.meta["missing"]:
+        lab = gpu["u"][l] >= 0.5
+        iou = (lab & truth[l]).sum() / max((lab | truth[l]).sum(), 1)
+        assert iou >= 0.8, (l, iou)
