@@ -60,10 +60,14 @@ struct seg4d {
     double *host_scal = nullptr;   // pinned mirror of scal
     unsigned *wave_ctrl = nullptr; // fused-sweep control block: 4 + tiles u32
     unsigned *host_wave = nullptr; // pinned: error flag of the last fused sweep
-    // mixed precision (allocated at the first solve with precision 1)
-    void *Wb = nullptr;            // bf16 [8][S] face weights by red end
-    float *gb = nullptr, *ib = nullptr;   // c / D_b and 1 / D_b, [2][S]
-    float *rho = nullptr, *dlt = nullptr; // r / D_b and the correction, [2][S]
+    // defect-correction solve (allocated at the first solve that needs them)
+    void *Wb = nullptr;            // mixed: bf16 [8][S] face weights by red end
+    float *gb = nullptr;           // mixed: c / D_b, [2][S]
+    float *ib = nullptr;           // 1 / D_b (mixed) or 1 / (D r) (FP32), [2][S]
+    float *rho = nullptr, *dlt = nullptr; // right-hand side and correction of the correction system
+    // FP32 solves (allocated at the first one): scaled weights, r = sqrt(gamma)
+    float *Ws = nullptr;           // [8][S] by red end
+    float *rs = nullptr;           // [2][S]
     int wave_T = 0;                // tiles per frame of the fused sweep
     int num_sms = 0;
     int wave_occ = 1;              // occupancy limit of the fused sweep (CTAs per SM)
@@ -82,7 +86,6 @@ struct seg4d {
     bool need_u0 = false;
     bool has_u = false;
     bool has_coef = false;
-    bool scaled = false;   // beta/gamma/diag/W hold the symmetrically scaled system
     std::string err;
 };
 
@@ -153,6 +156,7 @@ size_t bytes_for(const Layout &L, long long nv)
     b += 2 * S * sizeof(int);              // owner
     b += (size_t)nv * sizeof(float);       // staging
     b += 3 * kPartCap * sizeof(double) + 8 * sizeof(double);
+    b += 8 * S * sizeof(float) + 2 * S * sizeof(float) * 4;   // FP32 solve: Ws, rs, ib, rho, dlt
     return b;
 }
 
@@ -184,6 +188,8 @@ void free_all(seg4d *h)
     cudaFree(h->ib);
     cudaFree(h->rho);
     cudaFree(h->dlt);
+    cudaFree(h->Ws);
+    cudaFree(h->rs);
     cudaFree(h->seeds_d);
     cudaFree(h->stat_d);
     if (h->host_scal) cudaFreeHost(h->host_scal);
@@ -224,34 +230,75 @@ struct SolveOut {
     bool converged = false;
 };
 
-// Red-black SOR on x with the coefficients currently in beta/gamma/diag/W;
-// the brec per-block records of ||b||^2 must be in `partials` (written by
-// the coefficient kernel).  Stopping rule: ||b - A x||_2 <= tol ||b||_2, tested
-// before the first sweep and after every check_every sweeps.
-// With `mixed` (precision 1) every check is a defect pass (exact residual,
-// right-hand side of the BF16 correction system, delta = 0), the sweeps run
-// on A_b delta = r with BF16 weights and u += delta follows each batch.
-seg4d_status solve_loop(seg4d *h, float *x, const float *gam, double omega, double tol,
-                        int max_iters, int check_every, SolveOut &out, bool mixed)
+// Arrays of the defect-correction solve: rho (scaled right-hand side of the
+// correction system), dlt (the correction), ib; then Ws and rs (FP32: scaled
+// weights, r = sqrt(gamma)) or Wb and gb (mixed: BF16 weights, c / D_b).
+// Allocated at the first solve that needs them; the correction's padding
+// slots must read as zero.
+seg4d_status ensure_solve_arrays(seg4d *h, bool mixed)
+{
+    const size_t S2 = 2 * (size_t)h->L.S;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (*p) return true;
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return false;
+        }
+        return cudaMemsetAsync(*p, 0, bytes, h->stream) == cudaSuccess;
+    };
+    bool ok = alloc((void **)&h->rho, S2 * sizeof(float)) &&
+              alloc((void **)&h->dlt, S2 * sizeof(float)) &&
+              alloc((void **)&h->ib, S2 * sizeof(float));
+    if (ok && mixed)
+        ok = alloc(&h->Wb, 4 * S2 * sizeof(unsigned short)) &&
+             alloc((void **)&h->gb, S2 * sizeof(float));
+    if (ok && !mixed)
+        ok = alloc((void **)&h->Ws, 4 * S2 * sizeof(float)) &&
+             alloc((void **)&h->rs, S2 * sizeof(float));
+    if (!ok) return fail(h, SEG4D_ERR_OOM, "solve arrays: device allocation failed");
+    return SEG4D_OK;
+}
+
+// Red-black SOR for the system in beta/gamma/diag/W (its b = x on entry), as
+// defect correction: every check is an exact residual pass in flux form
+// (k_defect: r = b - A u from differences of the stored u, accurate far below
+// the FP32 noise of D (ubar - u)), the sweeps solve the correction system for
+// delta from 0, and u += delta follows each batch.  FP32 (precision 0): the
+// correction system is A itself, swept in its symmetrically scaled form
+// (Ws, r; see k_scaled_weights), u += r delta.  Mixed (precision 1): BF16
+// weights with the consistent diagonal D_b, u += delta.  The brec per-block
+// records of ||b||^2 must be in `partials` (written by the coefficient
+// kernel).  Stopping rule: ||b - A u||_2 <= tol ||b||_2, tested before the
+// first sweep and then at the spacing of next_check_batch.
+seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol, int max_iters,
+                          int check_every, SolveOut &out, bool mixed = false)
 {
     const Layout &L = h->L;
-    seg4d_status st = SEG4D_OK;
+    seg4d_status st = reduce_into(h, 0, brec);   // scal[0..2] = sum b^2, min b, max b
+    if (st) return st;
+    if ((st = ensure_solve_arrays(h, mixed))) return st;
+    if (mixed) {
+        launch_mixed_prepare(L, x, h->W, h->gamma, h->diag, h->Wb, h->gb, h->ib, h->beta,
+                             h->stream);
+        h->launches += 1;
+    } else {
+        launch_plain_prepare(L, x, h->gamma, h->diag, h->rs, h->ib, h->beta, h->stream);
+        launch_scaled_weights(L, h->W, h->Ws, h->gamma, h->stream);
+        h->launches += 2;
+    }
+    CK_LAUNCH("solve_prepare");
     int it = 0;
     bool timed_batch = false;
-    // checks spaced by next_check_batch (seg4d_internal.cuh)
     int batch = check_every;
     double prev_rn = -1.0;
     int prev_it = 0;
     bool wave_pending = false;
     for (;;) {
-        int nrec = kPartBlocks;
-        if (mixed)
-            nrec = launch_defect(L, x, h->beta, h->gamma, h->diag, h->W, h->ib, h->rho, h->dlt,
-                                 h->partials, h->stream);
-        else
-            nrec = launch_residual(L, x, h->beta, gam, h->diag, h->W, h->partials, h->stream);
+        const int nrec = launch_defect(L, x, h->beta, h->gamma, h->diag, h->W, h->ib, h->rho,
+                                       h->dlt, h->partials, h->stream);
         h->launches += 1;
-        CK_LAUNCH("residual");
+        CK_LAUNCH("defect");
         if ((st = reduce_into(h, 3, nrec))) return st;   // scal[3..5] = sum r^2, min u, max u
         if ((st = fetch_scal(h))) return st;
         if (wave_pending) {
@@ -289,28 +336,31 @@ seg4d_status solve_loop(seg4d *h, float *x, const float *gam, double omega, doub
                 launch_sweep_mixed(L, 0, h->dlt, h->rho, h->gb, h->Wb, (float)omega, h->stream);
                 launch_sweep_mixed(L, 1, h->dlt, h->rho, h->gb, h->Wb, (float)omega, h->stream);
             }
-            launch_apply(L, x, h->dlt, h->stream);
-            h->launches += 2LL * n + 1;
+            h->launches += 2LL * n;
             h->sweep_launches += 2LL * n;
-            CK_LAUNCH("sweep_mixed");
         } else if (h->p.sweep_variant == 0) {
             CK(cudaMemsetAsync(h->wave_ctrl, 0, (4 + h->wave_T) * sizeof(unsigned), h->stream));
             const int per_sm = std::min(h->p.ctas_per_sm > 0 ? h->p.ctas_per_sm : 4, h->wave_occ);
-            launch_sweep_wave(L, n, x, h->beta, gam, h->W, (float)omega, h->wave_ctrl,
+            launch_sweep_wave(L, n, h->dlt, h->rho, nullptr, h->Ws, (float)omega, h->wave_ctrl,
                               per_sm * h->num_sms, h->p.wait_test, h->stream);
             h->launches += 1;
             h->sweep_launches += 1;
-            CK_LAUNCH("sweep_wave");
         } else {
             for (int s = 0; s < n; ++s) {
-                launch_sweep(L, 0, x, h->beta, gam, h->W, (float)omega, h->stream);
-                launch_sweep(L, 1, x, h->beta, gam, h->W, (float)omega, h->stream);
+                launch_sweep(L, 0, h->dlt, h->rho, nullptr, h->Ws, (float)omega, h->stream);
+                launch_sweep(L, 1, h->dlt, h->rho, nullptr, h->Ws, (float)omega, h->stream);
             }
             h->launches += 2LL * n;
             h->sweep_launches += 2LL * n;
-            CK_LAUNCH("sweep");
         }
+        CK_LAUNCH("sweep");
         CK(cudaEventRecord(h->evs1, h->stream));
+        if (mixed)
+            launch_apply(L, x, h->dlt, h->stream);
+        else
+            launch_apply_scaled(L, x, h->dlt, h->rs, h->stream);
+        h->launches += 1;
+        CK_LAUNCH("apply");
         timed_batch = true;
         it += n;
         if (!mixed && h->p.sweep_variant == 0) {
@@ -320,49 +370,6 @@ seg4d_status solve_loop(seg4d *h, float *x, const float *gam, double omega, doub
             wave_pending = true;
         }
     }
-}
-
-// The solve of the system in beta/gamma/diag/W for x, with the ||b|| records
-// (brec of them) in `partials`.  Plain FP32 solves run on the symmetrically
-// scaled system (launch_scale_system: the sweeps read no gamma) and map x
-// back to u at the end; the arrays stay scaled until the next coefficient
-// kernel (read_field maps them back on demand).  Mixed solves run on the
-// original system.
-seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol, int max_iters,
-                          int check_every, SolveOut &out, bool mixed = false)
-{
-    seg4d_status st = reduce_into(h, 0, brec);   // scal[0..2] = sum b^2, min b, max b
-    if (st) return st;
-    h->scaled = false;
-    if (!mixed) {
-        launch_scale_system(h->L, x, h->beta, h->gamma, h->diag, h->W, false, h->stream);
-        h->launches += 2;
-        CK_LAUNCH("scale_system");
-        h->scaled = true;
-    }
-    st = solve_loop(h, x, mixed ? h->gamma : nullptr, omega, tol, max_iters, check_every, out,
-                    mixed);
-    if (!mixed && (st == SEG4D_OK || st == SEG4D_ERR_NOT_CONVERGED)) {
-        const int nrec = launch_unscale(h->L, x, h->gamma, h->partials, h->stream);
-        h->launches += 1;
-        CK_LAUNCH("unscale");
-        seg4d_status s2 = reduce_into(h, 3, nrec);   // scal[3..5] = sum u^2, min u, max u
-        if (!s2) s2 = fetch_scal(h);
-        if (s2) return s2;
-        out.umin = h->host_scal[4];
-        out.umax = h->host_scal[5];
-    }
-    return st;
-}
-
-// the step coefficients in beta/gamma/diag/W in their original form
-seg4d_status unscale_coefficients(seg4d *h)
-{
-    if (!h->scaled) return SEG4D_OK;
-    launch_scale_system(h->L, nullptr, h->beta, h->gamma, h->diag, h->W, true, h->stream);
-    CK_LAUNCH("scale_system");
-    h->scaled = false;
-    return SEG4D_OK;
 }
 
 seg4d_status upload_seeds(seg4d *h)
@@ -508,26 +515,6 @@ seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
     CK_LAUNCH("step_coef");
     h->has_coef = true;
     const bool mixed = h->p.precision == 1;
-    if (mixed) {
-        if (!h->Wb) {
-            const size_t S2 = 2 * (size_t)h->L.S;
-            if (cudaMalloc(&h->Wb, 4 * S2 * sizeof(unsigned short)) != cudaSuccess ||
-                cudaMalloc(&h->gb, S2 * sizeof(float)) != cudaSuccess ||
-                cudaMalloc(&h->ib, S2 * sizeof(float)) != cudaSuccess ||
-                cudaMalloc(&h->rho, S2 * sizeof(float)) != cudaSuccess ||
-                cudaMalloc(&h->dlt, S2 * sizeof(float)) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(h, SEG4D_ERR_OOM, "mixed precision arrays: allocation failed");
-            }
-            // padding slots of the correction must read as zero
-            CK(cudaMemsetAsync(h->dlt, 0, S2 * sizeof(float), h->stream));
-            CK(cudaMemsetAsync(h->Wb, 0, 4 * S2 * sizeof(unsigned short), h->stream));
-        }
-        launch_mixed_prepare(h->L, h->u, h->W, h->gamma, h->diag, h->Wb, h->gb, h->ib, h->beta,
-                             h->stream);
-        h->launches += 1;
-        CK_LAUNCH("mixed_prepare");
-    }
     SolveOut so;
     seg4d_status st = solve_system(h, h->u, brec, h->p.omega, h->p.tol, h->p.max_iters,
                                    h->p.check_every, so, mixed);
@@ -904,7 +891,6 @@ seg4d_status seg4d_read_field(seg4d *h, int field, float *dst, size_t n, int on_
     case SEG4D_FIELD_DIAG:
     case SEG4D_FIELD_OFF:
         if (!h->has_coef) return fail(h, SEG4D_ERR_STATE, "no step coefficients computed");
-        if ((st = unscale_coefficients(h))) return st;
         break;
     default:
         return fail(h, SEG4D_ERR_INVALID, "unknown field");

@@ -124,6 +124,52 @@ __global__ void __launch_bounds__(256, 2) k_defect(Layout L, const float *__rest
     block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
 }
 
+// Before an FP32 solve (the correction sweeps run on the scaled system, see
+// k_scaled_weights): per voxel r = sqrt(gamma), ib = 1 / (D r) (so that the
+// defect pass writes the scaled right-hand side rho = r_res / (D r)), and
+// beta <- x (= b, kept for the defect passes).  Padding slots (gamma = 0)
+// get r = ib = 0.
+__global__ void __launch_bounds__(256) k_plain_prepare(long long n4, const float4 *__restrict__ x,
+                                                       const float4 *__restrict__ gamma,
+                                                       const float4 *__restrict__ diag,
+                                                       float4 *__restrict__ rs,
+                                                       float4 *__restrict__ ib,
+                                                       float4 *__restrict__ beta)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n4;
+         e += (long long)gridDim.x * blockDim.x) {
+        const float4 g = gamma[e], d = diag[e];
+        const float *gp = &g.x, *dp = &d.x;
+        float4 r, iv;
+        float *rp = &r.x, *ip = &iv.x;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            rp[m] = gp[m] > 0.0f ? sqrtf(gp[m]) : 0.0f;
+            ip[m] = gp[m] > 0.0f ? 1.0f / (dp[m] * rp[m]) : 0.0f;
+        }
+        rs[e] = r;
+        ib[e] = iv;
+        beta[e] = x[e];
+    }
+}
+
+// u <- u + r delta (the FP32 solve's correction is in scaled units)
+__global__ void __launch_bounds__(256) k_apply_scaled(float4 *__restrict__ u,
+                                                      const float4 *__restrict__ delta,
+                                                      const float4 *__restrict__ rs, long long n4)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        float4 a = u[i];
+        const float4 b = delta[i], r = rs[i];
+        a.x = __fmaf_rn(r.x, b.x, a.x);
+        a.y = __fmaf_rn(r.y, b.y, a.y);
+        a.z = __fmaf_rn(r.z, b.z, a.z);
+        a.w = __fmaf_rn(r.w, b.w, a.w);
+        u[i] = a;
+    }
+}
+
 // u <- u + delta over both colour halves (padding holds 0 in both)
 __global__ void __launch_bounds__(256) k_apply(float4 *__restrict__ u,
                                                const float4 *__restrict__ delta, long long n4)
@@ -158,6 +204,30 @@ int launch_defect(const Layout &L, const float *u, const float *b, const float *
     k_defect<kVecF32><<<blocks, 256, 0, st>>>(L, u, b, gamma, diag, W, ib, rho, delta, partials,
                                               make_item_decode(L, nch), (unsigned)items);
     return blocks;
+}
+
+static int vec4_blocks(long long n4)
+{
+    long long blocks = (n4 + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    return (int)(blocks < 1 ? 1 : blocks);
+}
+
+void launch_plain_prepare(const Layout &L, const float *x, const float *gamma, const float *diag,
+                          float *rs, float *ib, float *beta, cudaStream_t st)
+{
+    const long long n4 = 2 * L.S / 4;   // P is a multiple of 4
+    k_plain_prepare<<<vec4_blocks(n4), 256, 0, st>>>(n4, (const float4 *)x, (const float4 *)gamma,
+                                                     (const float4 *)diag, (float4 *)rs,
+                                                     (float4 *)ib, (float4 *)beta);
+}
+
+void launch_apply_scaled(const Layout &L, float *u, const float *delta, const float *rs,
+                         cudaStream_t st)
+{
+    const long long n4 = 2 * L.S / 4;
+    k_apply_scaled<<<vec4_blocks(n4), 256, 0, st>>>((float4 *)u, (const float4 *)delta,
+                                                    (const float4 *)rs, n4);
 }
 
 void launch_apply(const Layout &L, float *u, const float *delta, cudaStream_t st)

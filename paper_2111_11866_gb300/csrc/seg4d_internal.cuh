@@ -121,7 +121,7 @@ void launch_smooth_coef(const Layout &L, const float *I, const double *h, double
 int launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,
                      double tau, double eps, float *beta, float *gamma, float *diag, float *W,
                      double *partials, cudaStream_t st);
-// gamma = NULL: the scaled system (G = 1)
+// gamma = NULL: a unit-diagonal (scaled) system, G = 1
 void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,
                   const float *W, float omega, cudaStream_t st);
 void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta,
@@ -142,17 +142,14 @@ void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *
 void launch_apply(const Layout &L, float *u, const float *delta, cudaStream_t st);
 int wave_tiles(const Layout &L);        // tiles per frame of the fused sweep
 int wave_max_ctas_per_sm();             // occupancy limit of the fused sweep
-// symmetric scaling of the system in beta/gamma/diag/W (and x, if not NULL)
-// to the unit-diagonal form the sweeps then solve with gamma = NULL, or back
-// (inverse); and x <- x r after a scaled solve, with records of x
-void launch_scale_system(const Layout &L, float *x, float *beta, float *gamma, float *diag,
-                         float *W, bool inverse, cudaStream_t st);
-int launch_unscale(const Layout &L, float *x, const float *r, double *partials, cudaStream_t st);
-// residual records of the step or presmoothing system (gamma = NULL: the
-// scaled system, G = 1); returns the number of per-block records written to
-// `partials` (at most kResBlocks)
-int launch_residual(const Layout &L, const float *x, const float *beta, const float *gamma,
-                    const float *diag, const float *W, double *partials, cudaStream_t st);
+// FP32 solves (see k_scaled_weights): scaled correction weights, per-voxel
+// r = sqrt(gamma), 1 / (D r), beta <- x; and u <- u + r delta
+void launch_scaled_weights(const Layout &L, const float *W, float *Ws, const float *gamma,
+                           cudaStream_t st);
+void launch_plain_prepare(const Layout &L, const float *x, const float *gamma, const float *diag,
+                          float *rs, float *ib, float *beta, cudaStream_t st);
+void launch_apply_scaled(const Layout &L, float *u, const float *delta, const float *rs,
+                         cudaStream_t st);
 void launch_reduce_partials(const double *partials, int nparts, double *out, cudaStream_t st);
 
 // Sweeps until the next stopping test of a solve.  After two checks with

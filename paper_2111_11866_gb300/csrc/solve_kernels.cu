@@ -301,90 +301,22 @@ void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta
                                                   test_wait);
 }
 
-// --------------------------------------------------------------- residual
-
-// r_v = b_v - (A u)_v = D_v (ubar_v - u_v) for every voxel, with ubar the
-// sweep's Gauss-Seidel value; records (sum r^2, min u, max u) per block.
-// Work item t = 2 * tile + colour, tile = one block of the sweep grid
-// (32 N slots x 8 rows at one (k, l)); blocks stride over the items.
-template <int N, bool kUnit>
-__global__ void __launch_bounds__(256, 3) k_residual_vec(
-    Layout L, const float *__restrict__ x, const float *__restrict__ beta,
-    const float *__restrict__ gamma, const float *__restrict__ diag, const float *__restrict__ W,
-    double *__restrict__ partials, ItemDecode dec, unsigned items)
-{
-    Rec3f a = rec3f_init();
-    for (unsigned t = blockIdx.x; t < items; t += gridDim.x) {
-        int C, chunk;
-        RowPos rp;
-        decode_item(dec, L, t, (int)(threadIdx.x >> 5), C, chunk, rp);
-        const int s0 = chunk * 32 * N + N * (int)(threadIdx.x & 31);
-        // whole warps leave together (rows past n2); lanes past the row end stay
-        // for the shuffles of gather_vec
-        if (rp.j >= L.n2) continue;
-        const bool act = s0 < L.P && 2 * s0 + (C ^ rp.p) < L.n1;
-        const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
-        const long long q = (long long)row * L.P + s0 + (C ? L.S : 0);
-        float Xs[N], Bp[N], Gp[N], Dp[N], acc[N];
-        ldv<N>(Xs, act, x + q);
-        ldv<N>(Bp, act, beta + q);
-        if (kUnit) {
-#pragma unroll
-            for (int m = 0; m < N; ++m) Gp[m] = 1.0f;
-        } else {
-            ldv<N>(Gp, act, gamma + q);
-        }
-        ldv<N>(Dp, act, diag + q);
-        if (C)
-            gather_vec<1, float, N>(L, x, W, act, row, s0, rp, acc);
-        else
-            gather_vec<0, float, N>(L, x, W, act, row, s0, rp, acc);
-        if (!act) continue;
-        const int e = C ^ rp.p;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            if (2 * (s0 + m) + e >= L.n1) continue;
-            const float ubar = __fmaf_rn(Gp[m], acc[m], Bp[m]);
-            const float res = __fmul_rn(Dp[m], __fsub_rn(ubar, Xs[m]));
-            rec3f_add(a, __fmul_rn(res, res), Xs[m]);
-        }
-    }
-    block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
-}
-
-int launch_residual(const Layout &L, const float *x, const float *beta, const float *gamma,
-                    const float *diag, const float *W, double *partials, cudaStream_t st)
-{
-    const int nch = (L.P + 32 * kVecF32 - 1) / (32 * kVecF32);
-    const long long items = item_count(L, nch);
-    const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
-    if (gamma)
-        k_residual_vec<kVecF32, false><<<blocks, 256, 0, st>>>(
-            L, x, beta, gamma, diag, W, partials, make_item_decode(L, nch), (unsigned)items);
-    else
-        k_residual_vec<kVecF32, true><<<blocks, 256, 0, st>>>(
-            L, x, beta, nullptr, diag, W, partials, make_item_decode(L, nch), (unsigned)items);
-    return blocks;
-}
-
 // ---------------------------------------------------- symmetric scaling
 
-// The step (or presmoothing) system D u - c sum_f w_f u_nb = b, divided by
-// c row by row, is M u = b / c with the symmetric M = diag(D/c) - W.  With
-// s = sqrt(D/c) = 1/sqrt(gamma) and v = s u it becomes (I - Wt) v = bt,
-//   Wt_f = w_f r_i r_nb(f),  bt = beta / r,  r = sqrt(gamma) = 1/s,
-// whose Gauss-Seidel / SOR iterates are those of the original system mapped
-// by v = u / r (row and variable scaling by positive diagonals).  A sweep
-// then reads bt and Wt and no gamma: one stream fewer per voxel-sweep.  The
-// residual of the original system is b - A u = (D r) (bt + sum_f Wt_f v_nb -
-// v), so diag holds D r.  `inverse` maps the arrays back.
+// The system D u - c sum_f w_f u_nb = b, divided by c row by row, is
+// M u = b / c with the symmetric M = diag(D/c) - W.  With r = sqrt(c/D) =
+// sqrt(gamma) and u = r v it becomes (I - Ws) v = b / (c / r) with unit
+// diagonal and Ws_f = w_f r_i r_nb(f); its Gauss-Seidel / SOR iterates are
+// the original ones mapped by u = r v (row and variable scaling by positive
+// diagonals).  The FP32 solve sweeps its correction system in this form, so a
+// sweep reads no per-voxel c/D.
 //
-// Face weights (red ends): w <-> w r_i r_nb on the interior faces of every red
-// voxel; r of both ends from gamma (sqrt of it, or gamma itself if inverse).
-__global__ void __launch_bounds__(256) k_scale_weights(Layout L, float *__restrict__ W,
-                                                       const float *__restrict__ gamma,
-                                                       bool inverse, ItemDecode dec,
-                                                       unsigned items)
+// Ws <- W r_i r_nb on the interior faces of every red voxel (0 on faces to the
+// boundary), r = sqrt(gamma) of both ends.
+__global__ void __launch_bounds__(256) k_scaled_weights(Layout L, const float *__restrict__ W,
+                                                        float *__restrict__ Ws,
+                                                        const float *__restrict__ gamma,
+                                                        ItemDecode dec, unsigned items)
 {
     for (unsigned t = blockIdx.x; t < items; t += gridDim.x) {
         int C, chunk;
@@ -402,101 +334,22 @@ __global__ void __launch_bounds__(256) k_scale_weights(Layout L, float *__restri
                                  q - dt, q + dt};
         const bool in[8] = {i >= 1, i + 1 < L.n1, rp.j > 0, rp.j + 1 < L.n2,
                             rp.k > 0, rp.k + 1 < L.n3, rp.l > 0, rp.l + 1 < L.n4};
-        const float gs = gamma[q];
-        const float rs = inverse ? gs : sqrtf(gs);
+        const float rs = sqrtf(gamma[q]);
 #pragma unroll
         for (int f = 0; f < 8; ++f) {
-            if (!in[f]) continue;
-            const float gn = gb[nb[f]];
-            const float rn = inverse ? gn : sqrtf(gn);
-            float *w = W + (long long)f * L.S + q;
-            *w = inverse ? *w / (rs * rn) : *w * rs * rn;
+            const long long o = (long long)f * L.S + q;
+            Ws[o] = in[f] ? W[o] * rs * sqrtf(gb[nb[f]]) : 0.0f;
         }
     }
 }
 
-// Per voxel: beta <-> beta / r, diag <-> D r, gamma <-> r, and (when x is
-// given) x <-> x / r, over both colours; padding slots (gamma = 0) untouched.
-__global__ void __launch_bounds__(256) k_scale_fields(long long n4, float4 *__restrict__ beta,
-                                                      float4 *__restrict__ gamma,
-                                                      float4 *__restrict__ diag,
-                                                      float4 *__restrict__ x, bool inverse)
-{
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n4;
-         e += (long long)gridDim.x * blockDim.x) {
-        float4 b = beta[e], g = gamma[e], d = diag[e], v = x ? x[e] : make_float4(0, 0, 0, 0);
-        float *bp = &b.x, *gp = &g.x, *dp = &d.x, *vp = &v.x;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            if (!(gp[m] > 0.0f)) continue;
-            const float r = inverse ? gp[m] : sqrtf(gp[m]);
-            bp[m] = inverse ? bp[m] * r : bp[m] / r;
-            dp[m] = inverse ? dp[m] / r : dp[m] * r;
-            gp[m] = inverse ? r * r : r;
-            vp[m] = inverse ? vp[m] * r : vp[m] / r;
-        }
-        beta[e] = b;
-        gamma[e] = g;
-        diag[e] = d;
-        if (x) x[e] = v;
-    }
-}
-
-// x <- x r (back to u) with records (sum x^2, min x, max x) of the result
-__global__ void __launch_bounds__(kPartThreads) k_unscale(long long n4, float4 *__restrict__ x,
-                                                          const float4 *__restrict__ r,
-                                                          double *__restrict__ partials)
-{
-    Rec3f a = rec3f_init();
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n4;
-         e += (long long)gridDim.x * blockDim.x) {
-        float4 v = x[e];
-        const float4 g = r[e];
-        float *vp = &v.x;
-        const float *gp = &g.x;
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-            if (gp[m] > 0.0f) {
-                vp[m] = vp[m] * gp[m];
-                rec3f_add(a, __fmul_rn(vp[m], vp[m]), vp[m]);
-            }
-        x[e] = v;
-    }
-    block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
-}
-
-static int elem_blocks(long long n4)
-{
-    long long b = (n4 + 255) / 256;
-    if (b > kPartBlocks) b = kPartBlocks;
-    return (int)(b < 1 ? 1 : b);
-}
-
-void launch_scale_system(const Layout &L, float *x, float *beta, float *gamma, float *diag,
-                         float *W, bool inverse, cudaStream_t st)
+void launch_scaled_weights(const Layout &L, const float *W, float *Ws, const float *gamma,
+                           cudaStream_t st)
 {
     const long long red_items = item_count(L, L.nchunk) / 2;
     const int blocks = (int)(red_items < kResBlocks ? red_items : kResBlocks);
-    const long long n4 = 2 * L.S / 4;   // P is a multiple of 4
-    if (inverse) {   // weights first: they need r before gamma goes back to r^2
-        k_scale_weights<<<blocks, 256, 0, st>>>(L, W, gamma, true, make_item_decode(L, L.nchunk),
-                                                (unsigned)red_items);
-        k_scale_fields<<<elem_blocks(n4), 256, 0, st>>>(n4, (float4 *)beta, (float4 *)gamma,
-                                                        (float4 *)diag, (float4 *)x, true);
-    } else {
-        k_scale_weights<<<blocks, 256, 0, st>>>(L, W, gamma, false,
-                                                make_item_decode(L, L.nchunk), (unsigned)red_items);
-        k_scale_fields<<<elem_blocks(n4), 256, 0, st>>>(n4, (float4 *)beta, (float4 *)gamma,
-                                                        (float4 *)diag, (float4 *)x, false);
-    }
-}
-
-int launch_unscale(const Layout &L, float *x, const float *r, double *partials, cudaStream_t st)
-{
-    const long long n4 = 2 * L.S / 4;
-    const int blocks = elem_blocks(n4);
-    k_unscale<<<blocks, kPartThreads, 0, st>>>(n4, (float4 *)x, (const float4 *)r, partials);
-    return blocks;
+    k_scaled_weights<<<blocks, 256, 0, st>>>(L, W, Ws, gamma, make_item_decode(L, L.nchunk),
+                                             (unsigned)red_items);
 }
 
 // Deterministic final reduction of the per-block records (one block).
