@@ -391,6 +391,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="arrival horizon of the serving measurement (0 = skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--mixed-steps", type=int, default=2,
+                    help="segmentations of the mixed-precision measurement (0 = skip)")
     ap.add_argument("--large-steps", type=int, default=20,
                     help="time steps of the large 512x512x128x48 grid (0 = skip)")
     ap.add_argument("--sweep-variant", type=int, default=1, choices=[0, 1],
@@ -493,28 +495,30 @@ def main():
     kernel_name = SWEEP_KERNELS[params.sweep_variant]
 
     # the same workload in mixed precision (same handle, same inputs)
-    u_plain = seg.read_u()
-    seg.set_params(precision=1)
-    one_step()
-    mixed_sweeps = 0
-    mixed_sweep_ms = 0.0
-    e0.record(stream)
-    for _ in range(max(1, min(args.steps, 2))):
-        info = one_step()
-        mixed_sweeps += info["sweeps_total"]
-        mixed_sweep_ms += info["sweep_ms"]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    mixed_ms = e0.elapsed_time(e1)
-    u_mixed = seg.read_u()
-    seg.set_params(precision=0)
-    nm = max(1, min(args.steps, 2))
-    mixed = {"value": nvox * mixed_sweeps / (mixed_ms / 1000.0), "unit": "voxel-sweeps/s",
-             "ms_per_step": mixed_ms / nm, "sweeps_per_segmentation": mixed_sweeps / nm,
-             "sweep_rate": nvox * mixed_sweeps / (mixed_sweep_ms / 1000.0),
-             "max_rel_diff_vs_f32": float(np.abs(u_mixed - u_plain).max() /
-                                          max(np.abs(u_plain).max(), 1e-30)),
-             "dtype": "bf16 sweep weights, f32 sweeps and defect passes, f64 norms"}
+    mixed = None
+    nm = min(args.steps, args.mixed_steps)
+    if nm > 0:
+        u_plain = seg.read_u()
+        seg.set_params(precision=1)
+        one_step()
+        mixed_sweeps = 0
+        mixed_sweep_ms = 0.0
+        e0.record(stream)
+        for _ in range(nm):
+            info = one_step()
+            mixed_sweeps += info["sweeps_total"]
+            mixed_sweep_ms += info["sweep_ms"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mixed_ms = e0.elapsed_time(e1)
+        u_mixed = seg.read_u()
+        seg.set_params(precision=0)
+        mixed = {"value": nvox * mixed_sweeps / (mixed_ms / 1000.0), "unit": "voxel-sweeps/s",
+                 "ms_per_step": mixed_ms / nm, "sweeps_per_segmentation": mixed_sweeps / nm,
+                 "sweep_rate": nvox * mixed_sweeps / (mixed_sweep_ms / 1000.0),
+                 "max_rel_diff_vs_f32": float(np.abs(u_mixed - u_plain).max() /
+                                              max(np.abs(u_plain).max(), 1e-30)),
+                 "dtype": "bf16 sweep weights, f32 sweeps and defect passes, f64 norms"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
