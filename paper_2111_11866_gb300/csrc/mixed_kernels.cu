@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__
 // max u).  b is the prepared beta array.  Work items and grid as the
 // residual kernel: item t = 2 * tile + colour over the sweep's tiles.
 template <int N>
-__global__ void __launch_bounds__(256, 2) k_defect(Layout L, const float *__restrict__ u,
+__global__ void __launch_bounds__(256, SEG4D_DEFECT_MINB) k_defect(Layout L, const float *__restrict__ u,
                                                    const float *__restrict__ b,
                                                    const float *__restrict__ gamma,
                                                    const float *__restrict__ diag,
@@ -198,11 +198,11 @@ int launch_defect(const Layout &L, const float *u, const float *b, const float *
                   const float *diag, const float *W, const float *ib, float *rho, float *delta,
                   double *partials, cudaStream_t st)
 {
-    const int nch = (L.P + 32 * kVecF32 - 1) / (32 * kVecF32);
+    const int nch = (L.P + 32 * kDefectN - 1) / (32 * kDefectN);
     const long long items = item_count(L, nch);
     const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
-    k_defect<kVecF32><<<blocks, 256, 0, st>>>(L, u, b, gamma, diag, W, ib, rho, delta, partials,
-                                              make_item_decode(L, nch), (unsigned)items);
+    k_defect<kDefectN><<<blocks, 256, 0, st>>>(L, u, b, gamma, diag, W, ib, rho, delta, partials,
+                                               make_item_decode(L, nch), (unsigned)items);
     return blocks;
 }
 

@@ -202,6 +202,15 @@ constexpr int kVecF32 = SEG4D_VEC_F32;
 constexpr int kVecBF16 = SEG4D_VEC_BF16;
 static_assert((kVecF32 == 2 || kVecF32 == 4) && (kVecBF16 == 2 || kVecBF16 == 4),
               "2 or 4 voxels per thread (P is a multiple of 4)");
+// voxels per thread of the single-grid defect pass (1, 2 or 4) and its resident
+// blocks per SM (3: measured faster than 2 and than one voxel per thread)
+#ifndef SEG4D_DEFECT_N
+#define SEG4D_DEFECT_N 2
+#endif
+#ifndef SEG4D_DEFECT_MINB
+#define SEG4D_DEFECT_MINB 3
+#endif
+constexpr int kDefectN = SEG4D_DEFECT_N;
 #ifndef SEG4D_VEC2_MINB
 #define SEG4D_VEC2_MINB 4
 #endif
@@ -209,14 +218,16 @@ static_assert((kVecF32 == 2 || kVecF32 == 4) && (kVecBF16 == 2 || kVecBF16 == 4)
 #define SEG4D_VEC4_MINB 2
 #endif
 template <int N>
-constexpr int vec_min_blocks() { return N == 2 ? SEG4D_VEC2_MINB : SEG4D_VEC4_MINB; }
+constexpr int vec_min_blocks() { return N == 1 ? 8 : (N == 2 ? SEG4D_VEC2_MINB : SEG4D_VEC4_MINB); }
 
 // N-wide vector loads (N = 2 or 4 consecutive slots, N-aligned) into float
 // arrays; a load whose condition is false yields zeros.
 template <int N>
 __device__ __forceinline__ void ldv(float (&v)[N], bool c, const float *p)
 {
-    if constexpr (N == 2) {
+    if constexpr (N == 1) {
+        v[0] = c ? *p : 0.0f;
+    } else if constexpr (N == 2) {
         const float2 t = c ? *reinterpret_cast<const float2 *>(p) : make_float2(0.0f, 0.0f);
         v[0] = t.x;
         v[1] = t.y;
@@ -233,7 +244,9 @@ __device__ __forceinline__ void ldv(float (&v)[N], bool c, const float *p)
 template <int N>
 __device__ __forceinline__ void ldv(float (&v)[N], bool c, const __nv_bfloat16 *p)
 {
-    if constexpr (N == 2) {
+    if constexpr (N == 1) {
+        v[0] = c ? __bfloat162float(*p) : 0.0f;
+    } else if constexpr (N == 2) {
         const unsigned t = c ? *reinterpret_cast<const unsigned *>(p) : 0u;
         v[0] = __uint_as_float(t << 16);
         v[1] = __uint_as_float(t & 0xFFFF0000u);
@@ -249,7 +262,9 @@ __device__ __forceinline__ void ldv(float (&v)[N], bool c, const __nv_bfloat16 *
 template <int N>
 __device__ __forceinline__ void stv(float *p, const float (&v)[N])
 {
-    if constexpr (N == 2)
+    if constexpr (N == 1)
+        *p = v[0];
+    else if constexpr (N == 2)
         *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
     else
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
