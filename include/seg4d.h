@@ -169,6 +169,23 @@ seg4d_status seg4d_set_seed(seg4d *h, const seg4d_seed *seeds, int nseeds);
  * pending re-initialisation from the seeds.  Errors: INVALID, CUDA. */
 seg4d_status seg4d_set_u(seg4d *h, const float *u, size_t n, int on_device);
 
+/* Dirichlet data on the ghost ring (Section 3.4, where the exact solution is
+ * prescribed on the ghost cells of the padded grid; zero is the default, the
+ * u^D = 0 of the segmentation runs).  The ring is given as its 8 face slabs:
+ * slab (d, side) holds the values at padded index 0 (side 0) or n_d + 1
+ * (side 1) along axis d (0 = x .. 3 = frame) for every padded position
+ * 0..n_e+1 of the other three axes, x fastest; the slabs follow each other in
+ * the order (0,0) (0,1) (1,0) (1,1) ... (3,1), and edges and corners repeat
+ * in several slabs with the same value.  g_prev is the data at t_{n-1}, which
+ * the face gradients of the coefficients see; g_now is the data at t_n, whose
+ * columns go to the right-hand side of the solve.  Both are copied (n =
+ * seg4d_dirichlet_count(dims) floats each) and used by every following
+ * solve / step until replaced; both NULL returns to zero data.
+ * Errors: INVALID (one NULL, n mismatch), OOM, CUDA. */
+size_t seg4d_dirichlet_count(const seg4d_dims *dims);
+seg4d_status seg4d_set_dirichlet(seg4d *h, const float *g_prev, const float *g_now, size_t n,
+                                 int on_device);
+
 /* Run the pending set-up now: thresholding, both presmoothing solves, face
  * coefficients G and, if pending, u0 and its rescale.  solve and step call it
  * themselves.  Errors: STATE (no image), NOT_CONVERGED (a presmoothing solve

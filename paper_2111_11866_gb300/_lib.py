@@ -74,6 +74,8 @@ SIGNATURES = {
     "seg4d_set_image": (C.c_int, [_P, _P, C.c_size_t, C.c_int]),
     "seg4d_set_seed": (C.c_int, [_P, C.POINTER(CSeed), C.c_int]),
     "seg4d_set_u": (C.c_int, [_P, _P, C.c_size_t, C.c_int]),
+    "seg4d_dirichlet_count": (C.c_size_t, [C.POINTER(CDims)]),
+    "seg4d_set_dirichlet": (C.c_int, [_P, _P, _P, C.c_size_t, C.c_int]),
     "seg4d_setup": (C.c_int, [_P, C.POINTER(CInfo)]),
     "seg4d_solve": (C.c_int, [_P, C.POINTER(CInfo)]),
     "seg4d_step": (C.c_int, [_P, C.c_int, C.POINTER(CInfo)]),
@@ -254,6 +256,23 @@ class Seg4D:
     def set_u(self, u):
         p, dev, keep = _ptr(u, self.nvox)
         self._check(self.lib.seg4d_set_u(self.h, p, self.nvox, dev))
+
+    @staticmethod
+    def dirichlet_count(dims) -> int:
+        n1, n2, n3, n4 = dims
+        return int(load().seg4d_dirichlet_count(C.byref(CDims(n1, n2, n3, n4))))
+
+    def set_dirichlet(self, g_prev=None, g_now=None):
+        """Ghost-ring Dirichlet data (seg4d_set_dirichlet); None, None = zero."""
+        if g_prev is None and g_now is None:
+            self._check(self.lib.seg4d_set_dirichlet(self.h, None, None, 0, 0))
+            return
+        n = self.dirichlet_count(self.dims)
+        p0, dev0, k0 = _ptr(g_prev, n)
+        p1, dev1, k1 = _ptr(g_now, n)
+        if dev0 != dev1:
+            raise ValueError("both ghost arrays on the host or both on the device")
+        self._check(self.lib.seg4d_set_dirichlet(self.h, p0, p1, n, dev0))
 
     def setup(self, allow_not_converged=False):
         info = CInfo()

@@ -68,6 +68,10 @@ struct seg4d {
     // FP32 solves (allocated at the first one): scaled weights, r = sqrt(gamma)
     float *Ws = nullptr;           // [8][S] by red end
     float *rs = nullptr;           // [2][S]
+    // Dirichlet data on the ghost ring (seg4d_set_dirichlet); zero when unset
+    float *gh_prev = nullptr, *gh_now = nullptr;
+    bool has_ghost = false;
+    Ghost ghost{};
     int wave_T = 0;                // tiles per frame of the fused sweep
     int num_sms = 0;
     int wave_occ = 1;              // occupancy limit of the fused sweep (CTAs per SM)
@@ -190,6 +194,8 @@ void free_all(seg4d *h)
     cudaFree(h->dlt);
     cudaFree(h->Ws);
     cudaFree(h->rs);
+    cudaFree(h->gh_prev);
+    cudaFree(h->gh_now);
     cudaFree(h->seeds_d);
     cudaFree(h->stat_d);
     if (h->host_scal) cudaFreeHost(h->host_scal);
@@ -260,7 +266,7 @@ seg4d_status ensure_solve_arrays(seg4d *h, bool mixed)
     return SEG4D_OK;
 }
 
-// Red-black SOR for the system in beta/gamma/diag/W (its b = x on entry), as
+// Red-black SOR for the system in beta (= b) / gamma / diag / W, as
 // defect correction: every check is an exact residual pass in flux form
 // (k_defect: r = b - A u from differences of the stored u, accurate far below
 // the FP32 noise of D (ubar - u)), the sweeps solve the correction system for
@@ -279,11 +285,10 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
     if (st) return st;
     if ((st = ensure_solve_arrays(h, mixed))) return st;
     if (mixed) {
-        launch_mixed_prepare(L, x, h->W, h->gamma, h->diag, h->Wb, h->gb, h->ib, h->beta,
-                             h->stream);
+        launch_mixed_prepare(L, h->W, h->gamma, h->diag, h->Wb, h->gb, h->ib, h->stream);
         h->launches += 1;
     } else {
-        launch_plain_prepare(L, x, h->gamma, h->diag, h->rs, h->ib, h->beta, h->stream);
+        launch_plain_prepare(L, h->gamma, h->diag, h->rs, h->ib, h->stream);
         launch_scaled_weights(L, h->W, h->Ws, h->gamma, h->stream);
         h->launches += 2;
     }
@@ -510,7 +515,8 @@ seg4d_status run_setup(seg4d *h, long long &sweeps)
 seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
 {
     const int brec = launch_step_coef(h->L, h->u, h->G, h->p.h, h->p.tau, h->p.eps, h->beta,
-                                      h->gamma, h->diag, h->W, h->partials, h->stream);
+                                      h->gamma, h->diag, h->W, h->partials,
+                                      h->has_ghost ? &h->ghost : nullptr, h->stream);
     h->launches += 1;
     CK_LAUNCH("step_coef");
     h->has_coef = true;
@@ -778,6 +784,63 @@ seg4d_status seg4d_set_u(seg4d *h, const float *u, size_t n, int on_device)
     CK(cudaStreamSynchronize(h->stream));
     h->has_u = true;
     h->need_u0 = false;
+    h->has_coef = false;
+    return SEG4D_OK;
+}
+
+size_t seg4d_dirichlet_count(const seg4d_dims *d)
+{
+    if (!dims_ok(d)) return 0;
+    const long long np[4] = {d->n1 + 2LL, d->n2 + 2LL, d->n3 + 2LL, d->n4 + 2LL};
+    long long total = 0;
+    for (int a = 0; a < 4; ++a) total += 2 * (np[0] * np[1] * np[2] * np[3] / np[a]);
+    return (size_t)total;
+}
+
+seg4d_status seg4d_set_dirichlet(seg4d *h, const float *g_prev, const float *g_now, size_t n,
+                                 int on_device)
+{
+    if (!h) return SEG4D_ERR_INVALID;
+    seg4d_status st = use_device(h);
+    if (st) return st;
+    if (!g_prev && !g_now) {
+        h->has_ghost = false;
+        return SEG4D_OK;
+    }
+    if (!g_prev || !g_now) return fail(h, SEG4D_ERR_INVALID, "give both ghost arrays, or neither");
+    const size_t need = seg4d_dirichlet_count(&h->dims);
+    if (n != need)
+        return fail(h, SEG4D_ERR_INVALID,
+                    "ghost data needs seg4d_dirichlet_count(dims) = " + std::to_string(need) +
+                        " floats per time level");
+    if (!h->gh_prev) {
+        if (cudaMalloc(&h->gh_prev, n * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&h->gh_now, n * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h->gh_prev);
+            h->gh_prev = h->gh_now = nullptr;
+            return fail(h, SEG4D_ERR_OOM, "ghost data: device allocation failed");
+        }
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(h->gh_prev, g_prev, n * sizeof(float), kind, h->stream));
+    CK(cudaMemcpyAsync(h->gh_now, g_now, n * sizeof(float), kind, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    Ghost &G = h->ghost;
+    G.prev = h->gh_prev;
+    G.now = h->gh_now;
+    const int nd[4] = {h->dims.n1, h->dims.n2, h->dims.n3, h->dims.n4};
+    long long off = 0;
+    for (int a = 0; a < 4; ++a) G.np[a] = nd[a] + 2;
+    for (int a = 0; a < 4; ++a) {
+        long long sz = 1;
+        for (int e = 0; e < 4; ++e)
+            if (e != a) sz *= G.np[e];
+        G.off[a] = off;
+        G.size[a] = sz;
+        off += 2 * sz;
+    }
+    h->has_ghost = true;
     h->has_coef = false;
     return SEG4D_OK;
 }

@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(256, 2) k_bcoef(const BWin *__restrict__ wins,
             else
                 coef_gather<0>(L, u, act, row, s, rp, u0, sm, sp, ed);
             if (!act) continue;
-            float wf[8], D, bt, gm;
-            coef_finish(K, g, u0, sm, sp, ed, wf, D, bt, gm);
+            float wf[8], D, bt, gm, cc;
+            coef_finish(K, g, u0, sm, sp, ed, wf, D, bt, gm, cc);
             if (C == 0)
 #pragma unroll
                 for (int f = 0; f < 8; ++f) W[(long long)f * L.S + q] = wf[f];

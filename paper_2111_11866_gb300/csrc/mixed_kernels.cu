@@ -40,16 +40,12 @@ namespace seg4d_impl {
 
 // After the FP32 coefficients: Wb = bf16(W) (red ends); per voxel
 // gamma_b = c / D_b, invD_b = 1 / D_b with D_b = D - c * excess, c = gamma*D.
-// The solve reads b itself (= u at the start of the step) instead of
-// beta = b / D, so beta is overwritten with u.
-__global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__restrict__ u,
-                                                       const float *__restrict__ W,
+__global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__restrict__ W,
                                                        const float *__restrict__ gamma,
                                                        const float *__restrict__ diag,
                                                        __nv_bfloat16 *__restrict__ Wb,
                                                        float *__restrict__ gb,
-                                                       float *__restrict__ ib,
-                                                       float *__restrict__ beta)
+                                                       float *__restrict__ ib)
 {
     MX_FOR_TILES(L, s, rp, row, {
         const long long q = (long long)row * L.P + s;
@@ -62,7 +58,6 @@ __global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__
             const float Db = D - c * ex;
             gb[C * L.S + q] = c / Db;
             ib[C * L.S + q] = 1.0f / Db;
-            beta[C * L.S + q] = u[C * L.S + q];
             if (C == 0)
                 for (int f = 0; f < 8; ++f)
                     Wb[(long long)f * L.S + q] = __float2bfloat16_rn(W[(long long)f * L.S + q]);
@@ -125,16 +120,14 @@ __global__ void __launch_bounds__(256, SEG4D_DEFECT_MINB) k_defect(Layout L, con
 }
 
 // Before an FP32 solve (the correction sweeps run on the scaled system, see
-// k_scaled_weights): per voxel r = sqrt(gamma), ib = 1 / (D r) (so that the
-// defect pass writes the scaled right-hand side rho = r_res / (D r)), and
-// beta <- x (= b, kept for the defect passes).  Padding slots (gamma = 0)
-// get r = ib = 0.
-__global__ void __launch_bounds__(256) k_plain_prepare(long long n4, const float4 *__restrict__ x,
+// k_scaled_weights): per voxel r = sqrt(gamma) and ib = 1 / (D r), so that
+// the defect pass writes the scaled right-hand side rho = r_res / (D r).
+// Padding slots (gamma = 0) get r = ib = 0.
+__global__ void __launch_bounds__(256) k_plain_prepare(long long n4,
                                                        const float4 *__restrict__ gamma,
                                                        const float4 *__restrict__ diag,
                                                        float4 *__restrict__ rs,
-                                                       float4 *__restrict__ ib,
-                                                       float4 *__restrict__ beta)
+                                                       float4 *__restrict__ ib)
 {
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n4;
          e += (long long)gridDim.x * blockDim.x) {
@@ -149,7 +142,6 @@ __global__ void __launch_bounds__(256) k_plain_prepare(long long n4, const float
         }
         rs[e] = r;
         ib[e] = iv;
-        beta[e] = x[e];
     }
 }
 
@@ -186,12 +178,10 @@ __global__ void __launch_bounds__(256) k_apply(float4 *__restrict__ u,
     }
 }
 
-void launch_mixed_prepare(const Layout &L, const float *u, const float *W, const float *gamma,
-                          const float *diag, void *Wb, float *gb, float *ib, float *beta,
-                          cudaStream_t st)
+void launch_mixed_prepare(const Layout &L, const float *W, const float *gamma, const float *diag,
+                          void *Wb, float *gb, float *ib, cudaStream_t st)
 {
-    k_mixed_prepare<<<kPartBlocks, 256, 0, st>>>(L, u, W, gamma, diag, (__nv_bfloat16 *)Wb, gb, ib,
-                                                 beta);
+    k_mixed_prepare<<<kPartBlocks, 256, 0, st>>>(L, W, gamma, diag, (__nv_bfloat16 *)Wb, gb, ib);
 }
 
 int launch_defect(const Layout &L, const float *u, const float *b, const float *gamma,
@@ -213,13 +203,13 @@ static int vec4_blocks(long long n4)
     return (int)(blocks < 1 ? 1 : blocks);
 }
 
-void launch_plain_prepare(const Layout &L, const float *x, const float *gamma, const float *diag,
-                          float *rs, float *ib, float *beta, cudaStream_t st)
+void launch_plain_prepare(const Layout &L, const float *gamma, const float *diag, float *rs,
+                          float *ib, cudaStream_t st)
 {
     const long long n4 = 2 * L.S / 4;   // P is a multiple of 4
-    k_plain_prepare<<<vec4_blocks(n4), 256, 0, st>>>(n4, (const float4 *)x, (const float4 *)gamma,
+    k_plain_prepare<<<vec4_blocks(n4), 256, 0, st>>>(n4, (const float4 *)gamma,
                                                      (const float4 *)diag, (float4 *)rs,
-                                                     (float4 *)ib, (float4 *)beta);
+                                                     (float4 *)ib);
 }
 
 void launch_apply_scaled(const Layout &L, float *u, const float *delta, const float *rs,

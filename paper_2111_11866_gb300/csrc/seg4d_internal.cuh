@@ -90,6 +90,20 @@ struct SeedStat {
     int pad;
 };
 
+// Dirichlet data on the ghost ring of the padded grid (indices -1 and n_d
+// along an axis), as the 8 face slabs of that ring: slab (d, side) holds the
+// values at padding index a_d = 0 (side 0) or n_d + 1 (side 1) for every
+// padded position of the other three axes (0..n_e+1, x fastest), slabs in the
+// order (0,0) (0,1) (1,0) ... (3,1).  Edges and corners of the ring lie in
+// several slabs; the one of the first axis out of range is read.  `prev` is
+// the data the coefficients see, `now` the data of the solve.
+struct Ghost {
+    const float *prev, *now;
+    long long off[4];   // offset of slab (d, 0); slab (d, 1) follows it
+    long long size[4];  // values per slab of axis d
+    int np[4];          // padded extents n_d + 2
+};
+
 // ---------------------------------------------------------------- launchers
 // set-up (setup_kernels.cu)
 void launch_split_from_natural(const Layout &L, const float *nat, float *split, cudaStream_t st);
@@ -117,10 +131,11 @@ void launch_smooth_coef(const Layout &L, const float *I, const double *h, double
                         int nparts, cudaStream_t st);
 
 // step and solve (solve_kernels.cu)
-// returns the number of per-block records (sum b^2, min b, max b) written
+// returns the number of per-block records (sum b^2, min b, max b) written;
+// ghost: Dirichlet data on the ghost ring (NULL: zero)
 int launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,
                      double tau, double eps, float *beta, float *gamma, float *diag, float *W,
-                     double *partials, cudaStream_t st);
+                     double *partials, const Ghost *ghost, cudaStream_t st);
 // gamma = NULL: a unit-diagonal (scaled) system, G = 1
 void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,
                   const float *W, float omega, cudaStream_t st);
@@ -128,10 +143,8 @@ void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta
                        const float *gamma, const float *W, float omega, unsigned *ctrl, int ctas,
                        int test_wait, cudaStream_t st);
 // mixed precision (mixed_kernels.cu); Wb is a __nv_bfloat16 [8][S] array
-// (launch_mixed_prepare overwrites beta with b = u, which launch_defect reads)
-void launch_mixed_prepare(const Layout &L, const float *u, const float *W, const float *gamma,
-                          const float *diag, void *Wb, float *gb, float *ib, float *beta,
-                          cudaStream_t st);
+void launch_mixed_prepare(const Layout &L, const float *W, const float *gamma, const float *diag,
+                          void *Wb, float *gb, float *ib, cudaStream_t st);
 // returns the number of per-block records written to `partials`
 int launch_defect(const Layout &L, const float *u, const float *b, const float *gamma,
                   const float *diag, const float *W, const float *ib, float *rho, float *delta,
@@ -143,11 +156,11 @@ void launch_apply(const Layout &L, float *u, const float *delta, cudaStream_t st
 int wave_tiles(const Layout &L);        // tiles per frame of the fused sweep
 int wave_max_ctas_per_sm();             // occupancy limit of the fused sweep
 // FP32 solves (see k_scaled_weights): scaled correction weights, per-voxel
-// r = sqrt(gamma), 1 / (D r), beta <- x; and u <- u + r delta
+// r = sqrt(gamma) and 1 / (D r); and u <- u + r delta
 void launch_scaled_weights(const Layout &L, const float *W, float *Ws, const float *gamma,
                            cudaStream_t st);
-void launch_plain_prepare(const Layout &L, const float *x, const float *gamma, const float *diag,
-                          float *rs, float *ib, float *beta, cudaStream_t st);
+void launch_plain_prepare(const Layout &L, const float *gamma, const float *diag, float *rs,
+                          float *ib, cudaStream_t st);
 void launch_apply_scaled(const Layout &L, float *u, const float *delta, const float *rs,
                          cudaStream_t st);
 void launch_reduce_partials(const double *partials, int nparts, double *out, cudaStream_t st);

@@ -433,7 +433,8 @@ void launch_face_G(const Layout &L, const float *Is0, const float *IsTH, const d
 // One implicit heat step of length sigma_t with zero-Neumann data:
 //   v + sum_{faces inside the grid} sigma_t/h_d^2 (v - v_nb) = I,
 // i.e. w_f = 1/h_d^2 on interior faces (0 on boundary faces), c = sigma_t,
-// D = 1 + c sum_f w_f, beta = I/D, gamma = c/D.  Records: (sum I^2, min, max).
+// D = 1 + c sum_f w_f, beta = I (the right-hand side), gamma = c/D.
+// Records: (sum I^2, min, max).
 __global__ void __launch_bounds__(kPartThreads) k_smooth_coef(Layout L, const float *__restrict__ I,
                                                               float4 inv_h2, float sigma_t,
                                                               float *__restrict__ beta,
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(kPartThreads) k_smooth_coef(Layout L, const fl
         const float D = 1.0f + sigma_t * wsum;
         const float b = I[C * L.S + q];
         diag[C * L.S + q] = D;
-        beta[C * L.S + q] = b / D;
+        beta[C * L.S + q] = b;
         gamma[C * L.S + q] = sigma_t / D;
         rec3f_add(a, __fmul_rn(b, b), b);
     }

@@ -369,9 +369,11 @@ void launch_reduce_partials(const double *partials, int nparts, double *out, cud
 }
 
 // Coefficients of the step system (coef_finish, Eq. new1) from
-// u = u^{resc,n-1} (also b).  Red voxels store their 8 w_f.  Records: (sum b^2, min b, max b).  Work
+// u = u^{resc,n-1}: w (red voxels store their 8), D, gamma = c/D, and b
+// itself in beta (u, plus the Dirichlet column of ghost data when given).  Records: (sum b^2, min b, max b).  Work
 // item t = 2 * tile + colour, tile = 32 slots x 8 rows at one (k, l), one
 // voxel per lane (coef_gather); blocks stride over the items.
+template <bool kGhost>
 __global__ void __launch_bounds__(256, 2) k_step_coef(Layout L, const float *__restrict__ u,
                                                       const float *__restrict__ G, StepConst K,
                                                       float *__restrict__ beta,
@@ -379,7 +381,7 @@ __global__ void __launch_bounds__(256, 2) k_step_coef(Layout L, const float *__r
                                                       float *__restrict__ diag,
                                                       float *__restrict__ W,
                                                       double *__restrict__ partials,
-                                                      ItemDecode dec, unsigned items)
+                                                      ItemDecode dec, unsigned items, Ghost gh)
 {
     Rec3f a = rec3f_init();
     for (unsigned t = blockIdx.x; t < items; t += gridDim.x) {
@@ -400,23 +402,41 @@ __global__ void __launch_bounds__(256, 2) k_step_coef(Layout L, const float *__r
         else
             coef_gather<0>(L, u, act, row, s, rp, u0, sm, sp, ed);
         if (!act) continue;
-        float w[8], D, bt, gm;
-        coef_finish(K, g, u0, sm, sp, ed, w, D, bt, gm);
+        const int i = 2 * s + (C ^ rp.p);
+        if (kGhost) apply_ghosts(gh, L, i, rp.j, rp.k, rp.l, sm, sp, ed);
+        float w[8], D, bt, gm, cc;
+        coef_finish(K, g, u0, sm, sp, ed, w, D, bt, gm, cc);
+        // b = u^{n-1}; with Dirichlet data, + c w_f g_f for every face to the
+        // ghost ring (the ghost value's column moved to the right-hand side)
+        float b = u0;
+        if (kGhost) {
+            const int c[4] = {i, rp.j, rp.k, rp.l};
+            const int nn[4] = {L.n1, L.n2, L.n3, L.n4};
+            float fold = 0.0f;
+#pragma unroll
+            for (int f = 0; f < 8; ++f) {
+                int e[4] = {c[0], c[1], c[2], c[3]};
+                e[f >> 1] += (f & 1) ? 1 : -1;
+                if (e[f >> 1] < 0 || e[f >> 1] >= nn[f >> 1])
+                    fold = __fmaf_rn(w[f], ghost_at(gh, gh.now, L, e[0], e[1], e[2], e[3]), fold);
+            }
+            b = __fmaf_rn(cc, fold, u0);
+        }
         const long long qc = (long long)C * L.S + q;
         if (C == 0)
 #pragma unroll
             for (int f = 0; f < 8; ++f) W[(long long)f * L.S + q] = w[f];
         diag[qc] = D;
-        beta[qc] = bt;
+        beta[qc] = b;
         gamma[qc] = gm;
-        rec3f_add(a, __fmul_rn(u0, u0), u0);
+        rec3f_add(a, __fmul_rn(b, b), b);
     }
     block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
 }
 
 int launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,
                      double tau, double eps, float *beta, float *gamma, float *diag, float *W,
-                     double *partials, cudaStream_t st)
+                     double *partials, const Ghost *ghost, cudaStream_t st)
 {
     StepConst K;
     for (int d = 0; d < 4; ++d) {
@@ -427,8 +447,14 @@ int launch_step_coef(const Layout &L, const float *u, const float *G, const doub
     K.eps2 = (float)(eps * eps);
     const long long items = item_count(L, L.nchunk);
     const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
-    k_step_coef<<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials,
-                                        make_item_decode(L, L.nchunk), (unsigned)items);
+    if (ghost)
+        k_step_coef<true><<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials,
+                                                  make_item_decode(L, L.nchunk), (unsigned)items,
+                                                  *ghost);
+    else
+        k_step_coef<false><<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials,
+                                                   make_item_decode(L, L.nchunk),
+                                                   (unsigned)items, Ghost{});
     return blocks;
 }
 

@@ -633,6 +633,56 @@ __device__ __forceinline__ void coef_gather(const Layout &L, const float *__rest
             for (int b = 0; b < 2; ++b) ed[3 + pp][a][b] = dg[pp][a][b];
 }
 
+__device__ __forceinline__ float ghost_at(const Ghost &G, const float *g, const Layout &L, int c0,
+                                          int c1, int c2, int c3)
+{
+    const int c[4] = {c0, c1, c2, c3};
+    const int n[4] = {L.n1, L.n2, L.n3, L.n4};
+    int d = 0;
+    while (d < 3 && c[d] >= 0 && c[d] < n[d]) ++d;
+    long long idx = G.off[d] + (c[d] < 0 ? 0 : G.size[d]), stride = 1;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (e == d) continue;
+        idx += (long long)(c[e] + 1) * stride;
+        stride *= G.np[e];
+    }
+    return g[idx];
+}
+
+// The gathered values of voxel (i, j, k, l) with the neighbours that lie on
+// the ghost ring taken from G.prev instead of zero.
+__device__ __forceinline__ void apply_ghosts(const Ghost &G, const Layout &L, int i, int j, int k,
+                                             int l, float (&sm)[4], float (&sp)[4],
+                                             float (&ed)[6][2][2])
+{
+    const int c[4] = {i, j, k, l};
+    const int n[4] = {L.n1, L.n2, L.n3, L.n4};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        int a[4] = {c[0], c[1], c[2], c[3]};
+        a[d] = c[d] - 1;
+        if (a[d] < 0) sm[d] = ghost_at(G, G.prev, L, a[0], a[1], a[2], a[3]);
+        a[d] = c[d] + 1;
+        if (a[d] >= n[d]) sp[d] = ghost_at(G, G.prev, L, a[0], a[1], a[2], a[3]);
+    }
+    int pi = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int t = d + 1; t < 4; ++t, ++pi)
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    int q[4] = {c[0], c[1], c[2], c[3]};
+                    q[d] += a ? 1 : -1;
+                    q[t] += b ? 1 : -1;
+                    if (q[d] < 0 || q[d] >= n[d] || q[t] < 0 || q[t] >= n[t])
+                        ed[pi][a][b] = ghost_at(G, G.prev, L, q[0], q[1], q[2], q[3]);
+                }
+}
+
 // Step coefficients of one voxel (Eq. new1) from its gathered values and
 // its 8 face edge coefficients g: A_f = sqrt(eps^2 + |grad^f u|^2),
 // Abar = sqrt(eps^2 + (1/8) sum_f |grad^f u|^2), w_f = G_f / (A_f h_d^2),
@@ -644,7 +694,7 @@ __device__ __forceinline__ void coef_gather(const Layout &L, const float *__rest
 __device__ __forceinline__ void coef_finish(const StepConst &K, const float (&g)[8], float u0,
                                             const float (&sm)[4], const float (&sp)[4],
                                             const float (&ed)[6][2][2], float (&w)[8],
-                                            float &D, float &bt, float &gm)
+                                            float &D, float &bt, float &gm, float &cc)
 {
     float g2[8];
     face_grad_sq8_from(u0, sm, sp, ed, K.inv_h, g2);
@@ -652,7 +702,7 @@ __device__ __forceinline__ void coef_finish(const StepConst &K, const float (&g)
 #pragma unroll
     for (int f = 0; f < 8; ++f) sum += g2[f];
     const float Abar = sqrtf(K.eps2 + 0.125f * sum);
-    const float cc = K.tau * Abar;
+    cc = K.tau * Abar;
     float wsum = 0.0f;
 #pragma unroll
     for (int f = 0; f < 8; ++f) {
