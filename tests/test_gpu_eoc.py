@@ -5,9 +5,8 @@ u = (|x|^2 - 1)/6 + t of the 4D level-set flow on [-1.25, 1.25]^4 as initial
 condition and as Dirichlet data on the ghost cells (seg4d_set_dirichlet),
 tau = h^2 and the eps = h reading of the table (the same reading the oracle's
 pin uses).  At N = 10, 20, 40 the GPU's error must equal the FP64 oracle's up
-to the FP32 solve; at N = 80, past what the oracle runs in a test, the order
-40 -> 80 must match the printed table's row, and the absolute error the
-printed one up to the same constant factor the oracle shows at N <= 40.
+to the FP32 solve.  At N = 80 and 160, past what the oracle runs in a test,
+the orders are checked against the printed rows (see the tests for row 5).
 """
 import math
 import os
@@ -49,22 +48,24 @@ def _exact(coords, t):
     return (s - 1.0) / 6.0 + t
 
 
-def _ghosts(n, h, t):
-    """The 8 face slabs of the padded grid (seg4d_set_dirichlet's layout):
-    padded index a in 0..n+1 sits at x(a) = -L + (a - 1/2) h."""
-    x = -L_HALF + (np.arange(n + 2) - 0.5) * h
+def _ghosts(n, h, t, dev):
+    """The 8 face slabs of the padded grid (seg4d_set_dirichlet's layout),
+    built on the device: padded index a in 0..n+1 sits at x(a) = -L + (a - 1/2) h."""
+    import torch
+    x = -L_HALF + (torch.arange(n + 2, device=dev, dtype=torch.float64) - 0.5) * h
     out = []
     for d in range(4):
         for side in (0, n + 1):
-            axes = []
-            for e in (3, 2, 1, 0):          # slowest first, x fastest
-                axes.append(np.array([x[side]]) if e == d else x)
-            grids = np.meshgrid(*axes, indexing="ij")
-            out.append(_exact(grids, t).astype(np.float32).ravel())
-    return np.concatenate(out)
+            axes = [x[side:side + 1] if e == d else x for e in (3, 2, 1, 0)]   # x fastest
+            grids = torch.meshgrid(*axes, indexing="ij")
+            out.append(_exact(grids, t).to(torch.float32).reshape(-1))
+    return torch.cat(out)
 
 
 def _gpu_eoc(n, steps, tol=1e-6):
+    """L2((0,T), L2) error of the GPU run; ghosts, u0 and errors on the device."""
+    import torch
+    dev = torch.device("cuda")
     h = 2.0 * L_HALF / n
     tau = T_END / steps
     p = _lib.Params.defaults()
@@ -74,20 +75,23 @@ def _gpu_eoc(n, steps, tol=1e-6):
     p.delta = p.vartheta = 0.0
     p.tol = tol
     dims = (n, n, n, n)
-    xc = -L_HALF + (np.arange(1, n + 1) - 0.5) * h
-    grid = np.meshgrid(xc, xc, xc, xc, indexing="ij")   # (l, k, j, i)
+    xc = -L_HALF + (torch.arange(1, n + 1, device=dev, dtype=torch.float64) - 0.5) * h
+    r2 = (xc[:, None, None, None] ** 2 + xc[None, :, None, None] ** 2 +
+          xc[None, None, :, None] ** 2 + xc[None, None, None, :] ** 2)
+    u = torch.empty((n, n, n, n), device=dev, dtype=torch.float32)
     err2 = 0.0
     with _lib.Seg4D(dims, params=p) as s:
-        s.set_image(np.zeros((n, n, n, n), np.float32))
+        s.set_image(torch.zeros((n, n, n, n), device=dev, dtype=torch.float32))
         s.set_seeds([])
         s.setup()
-        s.set_u(_exact(grid, 0.0).astype(np.float32))
-        assert s.dirichlet_count(dims) == _ghosts(n, h, 0.0).size
+        s.set_u(((r2 - 1.0) / 6.0).to(torch.float32))
+        assert s.dirichlet_count(dims) == _ghosts(n, h, 0.0, dev).numel()
         for k in range(1, steps + 1):
-            s.set_dirichlet(_ghosts(n, h, (k - 1) * tau), _ghosts(n, h, k * tau))
+            s.set_dirichlet(_ghosts(n, h, (k - 1) * tau, dev), _ghosts(n, h, k * tau, dev))
             info = s.solve()
             assert info["status"] == _lib.OK and info["res_rel"] <= tol, info
-            e = s.read_u().astype(np.float64) - _exact(grid, k * tau)
+            s.read_u(u)
+            e = u.to(torch.float64) - ((r2 - 1.0) / 6.0 + k * tau)
             err2 += tau * h ** 4 * float((e * e).sum())
     return math.sqrt(err2)
 
@@ -101,11 +105,30 @@ def test_gpu_eoc_error_equals_oracle(n):
     assert abs(gpu - ref) <= 2e-3 * ref, (n, gpu, ref)
 
 
-def test_gpu_eoc_order_at_80_matches_table():
+@pytest.fixture(scope="module")
+def gpu_errs():
+    """Errors at N = 40 (1e-6 is far below its discretisation error), 80 and
+    160 (solved to 3e-7: at N = 160 a 1e-6 solve changes the error by tens of
+    percent)."""
     table = _table()
-    e40 = _gpu_eoc(40, table[40][1])
-    e80 = _gpu_eoc(80, table[80][1])
-    eoc = math.log2(e40 / e80)
+    return {40: _gpu_eoc(40, table[40][1]), 80: _gpu_eoc(80, table[80][1], tol=3e-7),
+            160: _gpu_eoc(160, table[160][1], tol=3e-7)}
+
+
+def test_gpu_eoc_order_40_80_matches_table(gpu_errs):
+    """Row 4 of the table (N = 80: 41M voxels, 64 steps), past what the oracle
+    runs in a test; absolute errors the printed ones up to the oracle's factor."""
+    table = _table()
+    eoc = math.log2(gpu_errs[40] / gpu_errs[80])
     assert abs(eoc - table[80][3]) < 0.05, (eoc, table[80][3])
-    ratio = table[80][2] / e80
-    assert 2.2 < ratio < 2.7, ratio
+    ratios = [table[n][2] / gpu_errs[n] for n in (40, 80)]
+    assert all(2.2 < r < 2.7 for r in ratios), ratios
+
+
+def test_gpu_eoc_order_80_160_is_second_order(gpu_errs):
+    """Row 5 (N = 160: 655M voxels, 256 steps).  The table prints 1.861 there;
+    solved to 3e-7 the scheme is second order (about 2.03).  The printed value
+    is matched only by looser solves (1e-6 gives about 1.78): at N = 160 the
+    row depends on the solve tolerance, which the paper does not give."""
+    eoc = math.log2(gpu_errs[80] / gpu_errs[160])
+    assert 1.9 < eoc < 2.15, eoc
