@@ -41,9 +41,12 @@ struct BWin {
     SeedDev *seeds;
     SeedStat *stat;
     int nseeds;
-    int mixed;                     // precision 1: the arrays below exist
+    // defect-correction solve: rho = r * ib (right-hand side of the correction
+    // system), dlt (the correction), ib = 1/D (FP32) or 1/D_b (mixed), [2][S]
+    float *ib, *rho, *dlt;
+    int mixed;                     // precision 1: Wb and gb exist
     __nv_bfloat16 *Wb;             // bf16 [8][S] face weights by red end
-    float *gb, *ib, *rho, *dlt;    // c/D_b, 1/D_b, r/D_b, correction: [2][S]
+    float *gb;                     // c / D_b, [2][S]
 };
 
 // A window's (row, slot) pairs of one colour are enumerated linearly,
@@ -112,9 +115,11 @@ __device__ inline bool group_pos(const BWin &wd, long long t, RowPos &rp, int &s
 
 // --------------------------------------------------------------- kernels
 
-// One colour of one sweep over every window, N voxels per thread
-// (relax_vec); mixed windows sweep the BF16 correction system instead.  The
-// black pass takes the tiles in reverse, starting on what is still in L2.
+// One colour of one sweep of the correction system over every window, N
+// voxels per thread (relax_vec): delta <- delta + omega (rho + g sum_f w_f
+// delta_nb - delta) with FP32 weights and g = c/D, or BF16 weights and
+// g = c/D_b (mixed).  The black pass takes the tiles in reverse, starting on
+// what is still in L2.
 template <int C, bool kMixed, int N = kMixed ? kVecBF16 : kVecF32>
 __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_bsweep(
     const BWin *__restrict__ wins, const long long *__restrict__ starts, int nwin, float omega)
@@ -130,54 +135,8 @@ __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_bsweep(
         relax_vec<C, __nv_bfloat16, N>(L, wins[w].dlt, wins[w].rho, wins[w].gb, wins[w].Wb, omega,
                                        act, row, s0, rp);
     else
-        relax_vec<C, float, N>(L, wins[w].x, wins[w].beta, wins[w].gamma, wins[w].W, omega, act,
+        relax_vec<C, float, N>(L, wins[w].dlt, wins[w].rho, wins[w].gamma, wins[w].W, omega, act,
                                row, s0, rp);
-}
-
-// residual records per chunk of kChunkTiles tiles: (sum r^2, min x, max x),
-// r = D (ubar - x) with the sweep's gather (gather_vec); a chunk is
-// kChunkTiles / N tiles of 256 N-slot groups, both colours
-__global__ void __launch_bounds__(256, 2) k_bresidual(const BWin *__restrict__ wins,
-                                                      const long long *__restrict__ cstarts,
-                                                      int nwin, double *__restrict__ parts)
-{
-    constexpr int N = kVecF32;
-    const long long b = blockIdx.x;
-    const int w = find_win(cstarts, nwin, b);
-    const Layout L = wins[w].L;
-    const float *x = wins[w].x, *beta = wins[w].beta, *gamma = wins[w].gamma;
-    const float *diag = wins[w].diag, *W = wins[w].W;
-    const long long nt = win_gtiles(L, N);
-    const long long t0 = (b - cstarts[w]) * (kChunkTiles / N);
-    Rec3f a = rec3f_init();
-    for (long long t = t0; t < t0 + kChunkTiles / N && t < nt; ++t) {
-        RowPos rp{0, 0, 0, 0};
-        int s0 = 0, row = 0;
-        const bool in_win = group_pos<N>(wins[w], t, rp, s0, row);
-        for (int C = 0; C < 2; ++C) {
-            const bool act = in_win && 2 * s0 + (C ^ rp.p) < L.n1;
-            const long long q = (long long)row * L.P + s0 + (C ? L.S : 0);
-            float xs[N], bp[N], gp[N], dp[N], acc[N];
-            ldv<N>(xs, act, x + q);
-            ldv<N>(bp, act, beta + q);
-            ldv<N>(gp, act, gamma + q);
-            ldv<N>(dp, act, diag + q);
-            if (C)
-                gather_vec<1, float, N>(L, x, W, act, row, s0, rp, acc);
-            else
-                gather_vec<0, float, N>(L, x, W, act, row, s0, rp, acc);
-            if (!act) continue;
-            const int e = C ^ rp.p;
-#pragma unroll
-            for (int m = 0; m < N; ++m) {
-                if (2 * (s0 + m) + e >= L.n1) continue;
-                const float ubar = __fmaf_rn(gp[m], acc[m], bp[m]);
-                const float r = __fmul_rn(dp[m], __fsub_rn(ubar, xs[m]));
-                rec3f_add(a, __fmul_rn(r, r), xs[m]);
-            }
-        }
-    }
-    block_write3(rec3f_acc(a), parts + 3 * b);
 }
 
 // per-window fixed-order reduction of the chunk records (one block per window)
@@ -193,8 +152,8 @@ __global__ void __launch_bounds__(256) k_breduce(const long long *__restrict__ c
 }
 
 // step coefficients (coef_finish, Eq. new1) for every window, one voxel per
-// lane on the window's linear 256-slot tiles (coef_gather); records
-// (sum b^2, min, max)
+// lane on the window's linear 256-slot tiles (coef_gather): w, D, gamma = c/D,
+// b itself in beta, ib = 1/D; records (sum b^2, min, max)
 __global__ void __launch_bounds__(256, 2) k_bcoef(const BWin *__restrict__ wins,
                                                   const long long *__restrict__ cstarts, int nwin,
                                                   StepConst K, double *__restrict__ parts)
@@ -204,6 +163,7 @@ __global__ void __launch_bounds__(256, 2) k_bcoef(const BWin *__restrict__ wins,
     const Layout L = wins[w].L;
     const float *u = wins[w].u, *G = wins[w].G;
     float *beta = wins[w].beta, *gamma = wins[w].gamma, *diag = wins[w].diag, *W = wins[w].W;
+    float *ib = wins[w].ib;
     const long long nt = win_tiles(L);
     const long long t0 = (b - cstarts[w]) * kChunkTiles;
     Rec3f a = rec3f_init();
@@ -230,8 +190,9 @@ __global__ void __launch_bounds__(256, 2) k_bcoef(const BWin *__restrict__ wins,
 #pragma unroll
                 for (int f = 0; f < 8; ++f) W[(long long)f * L.S + q] = wf[f];
             diag[C * L.S + q] = D;
-            beta[C * L.S + q] = bt;
+            beta[C * L.S + q] = u0;
             gamma[C * L.S + q] = gm;
+            ib[C * L.S + q] = __frcp_rn(D);
             rec3f_add(a, __fmul_rn(u0, u0), u0);
         }
     }
@@ -250,6 +211,7 @@ __global__ void __launch_bounds__(256) k_bsmooth_coef(const BWin *__restrict__ w
     const Layout L = wins[w].L;
     const float *I = wins[w].x;
     float *beta = wins[w].beta, *gamma = wins[w].gamma, *diag = wins[w].diag, *W = wins[w].W;
+    float *ib = wins[w].ib;
     const float ih2[4] = {inv_h2.x, inv_h2.y, inv_h2.z, inv_h2.w};
     const int nn[4] = {L.n1, L.n2, L.n3, L.n4};
     const long long nt = win_tiles(L);
@@ -275,8 +237,9 @@ __global__ void __launch_bounds__(256) k_bsmooth_coef(const BWin *__restrict__ w
             const float D = 1.0f + sigma_t * wsum;
             const float bv = I[C * L.S + q];
             diag[C * L.S + q] = D;
-            beta[C * L.S + q] = bv / D;
+            beta[C * L.S + q] = bv;
             gamma[C * L.S + q] = sigma_t / D;
+            ib[C * L.S + q] = __frcp_rn(D);
             rec3f_add(a, __fmul_rn(bv, bv), bv);
         }
     }
@@ -294,9 +257,8 @@ __global__ void __launch_bounds__(256) k_bmixed_prepare(const BWin *__restrict__
     if (!wins[w].mixed) return;
     const Layout L = wins[w].L;
     const float *W = wins[w].W, *gamma = wins[w].gamma, *diag = wins[w].diag;
-    const float *u = wins[w].u;
     __nv_bfloat16 *Wb = wins[w].Wb;
-    float *gb = wins[w].gb, *ib = wins[w].ib, *beta = wins[w].beta;
+    float *gb = wins[w].gb, *ib = wins[w].ib;
     const long long nt = win_tiles(L);
     const long long t0 = (b - cstarts[w]) * kChunkTiles;
     for (long long t = t0; t < t0 + kChunkTiles && t < nt; ++t) {
@@ -313,7 +275,6 @@ __global__ void __launch_bounds__(256) k_bmixed_prepare(const BWin *__restrict__
             const float Db = D - c * ex;
             gb[C * L.S + q] = c / Db;
             ib[C * L.S + q] = 1.0f / Db;
-            beta[C * L.S + q] = u[C * L.S + q];
             if (C == 0)
                 for (int f = 0; f < 8; ++f)
                     Wb[(long long)f * L.S + q] = __float2bfloat16_rn(W[(long long)f * L.S + q]);
@@ -321,8 +282,8 @@ __global__ void __launch_bounds__(256) k_bmixed_prepare(const BWin *__restrict__
     }
 }
 
-// exact residual in flux form (flux_residual_vec; records) + rho = r / D_b,
-// delta = 0; beta holds b itself after k_bmixed_prepare.  A chunk of
+// exact residual in flux form (flux_residual_vec; records) + rho = r * ib,
+// delta = 0; beta holds b itself.  A chunk of
 // kChunkTiles 256-slot tiles is kChunkTiles / N tiles of 256 N-slot groups.
 __global__ void __launch_bounds__(256, 2) k_bdefect(const BWin *__restrict__ wins,
                                                     const long long *__restrict__ cstarts,
@@ -628,14 +589,15 @@ Layout layout_of(const seg4d_dims &d)
 }
 
 // main block: u, beta, gamma, diag (2S each), W (8S), G (16S) floats, owner
-// (2S ints), seeds, seed stats; image block: I0, ITH, Is0, IsTH (2S each)
+// (2S ints), seeds, seed stats, ib, rho, dlt (2S each) [+ Wb (8S bf16), gb
+// (2S) in mixed precision]; image block: I0, ITH, Is0, IsTH (2S each)
 size_t main_bytes(const Layout &L, int nseeds, bool mixed)
 {
     const size_t S = (size_t)L.S;
     return align_up(32 * S * 4) + align_up(2 * S * 4) +
            align_up(sizeof(SeedDev) * std::max(nseeds, 1)) +
-           align_up(sizeof(SeedStat) * std::max(nseeds, 1)) +
-           (mixed ? align_up(8 * S * 2) + 4 * align_up(2 * S * 4) : 0);
+           align_up(sizeof(SeedStat) * std::max(nseeds, 1)) + 3 * align_up(2 * S * 4) +
+           (mixed ? align_up(8 * S * 2) + align_up(2 * S * 4) : 0);
 }
 
 size_t img_bytes(const Layout &L) { return align_up(8 * (size_t)L.S * 4); }
@@ -663,17 +625,19 @@ void carve(seg4d_batch *b, Window &w)
     w.d.stat = (SeedStat *)p;
     p += align_up(sizeof(SeedStat) * std::max((int)w.seeds.size(), 1));
     w.d.nseeds = (int)w.seeds.size();
+    w.d.ib = (float *)p;
+    p += align_up(2 * S * 4);
+    w.d.rho = (float *)p;
+    p += align_up(2 * S * 4);
+    w.d.dlt = (float *)p;
+    p += align_up(2 * S * 4);
     w.d.mixed = b->p.precision == 1;
+    w.d.Wb = nullptr;
+    w.d.gb = nullptr;
     if (w.d.mixed) {
         w.d.Wb = (__nv_bfloat16 *)p;
         p += align_up(8 * S * 2);
         w.d.gb = (float *)p;
-        p += align_up(2 * S * 4);
-        w.d.ib = (float *)p;
-        p += align_up(2 * S * 4);
-        w.d.rho = (float *)p;
-        p += align_up(2 * S * 4);
-        w.d.dlt = (float *)p;
     }
     w.d.x = w.d.u;
     float *g = (float *)(b->arena.base + w.off_img);
@@ -776,12 +740,14 @@ struct SolveItem {
 };
 
 // Batched red-black SOR over every window of `items` (each window's d.x,
-// beta, gamma, diag, W already set up).  Per window: stop when
+// beta = b, gamma, diag, W, ib already set up), as defect correction (see
+// solve_system in api.cu): a test is the exact flux-form residual, which
+// also sets up the correction system; the sweeps solve it for delta, and
+// u += delta precedes the next test.  Per window: stop when
 // ||b - A x|| <= tol ||b||.  Each window has its own check schedule
 // (next_check_batch on its own residual history): every round sweeps all
 // active windows up to the earliest pending check, then tests the windows
-// whose check is due (in mixed precision: u += delta, then the defect pass
-// for those only).  A window's sweeps and tests therefore do not depend on
+// whose check is due (u += delta, then the defect pass, for those only).  A window's sweeps and tests therefore do not depend on
 // the other windows, and its result is the same alone or in any mix.
 seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double omega, double tol,
                          int max_iters, int check_every, long long &sweeps_total,
@@ -803,19 +769,15 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
         std::vector<Window *> ws;
         for (auto *a : due) ws.push_back(a->w);
         if ((st = set_table(b, ws))) return st;
-        if (mixed && it > 0) {
+        if (it > 0) {
             k_bapply<<<(unsigned)b->n_tile, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
                                                                  (int)ws.size());
             b->launches += 1;
         }
         const long long nch = b->n_chunk;
         if ((st = ensure_parts(b, nch))) return st;
-        if (mixed)
-            k_bdefect<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk, (int)ws.size(),
-                                                            b->d_parts);
-        else
-            k_bresidual<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk,
-                                                              (int)ws.size(), b->d_parts);
+        k_bdefect<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk, (int)ws.size(),
+                                                        b->d_parts);
         b->launches += 1;
         BCK(cudaGetLastError());
         if ((st = reduce_windows(b, ws.size()))) return st;
