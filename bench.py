@@ -275,6 +275,63 @@ def run_large(nsteps, params, local):
         torch.cuda.empty_cache()
 
 
+def run_paper_scale(nsteps, params, local):
+    """A grid of the size of the paper's largest stack (567x577x147 x 70
+    frames, 3.37G voxels; the paper ran it on six nodes with 1012 GB) on one
+    GPU with a lean handle (80 B/voxel): synthetic nuclei made frame by frame
+    on the device into a host buffer, set-up, then `nsteps` time steps."""
+    import numpy as np
+    import torch
+    from paper_2111_11866_gb300 import _lib, synth
+
+    dims, seeds, count, frames = synth.paper_scale("cuda")
+    n1, n2, n3, n4 = dims
+    stream = torch.cuda.current_stream()
+    seg = _lib.Seg4D(dims, stream=stream, params=params, lean=True)
+    try:
+        host = np.empty((n4, n3, n2, n1), np.float32)
+        t0 = time.perf_counter()
+        for l, f in enumerate(frames):
+            host[l] = f.cpu().numpy()
+        t_gen = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+        seg.set_image(host)
+        del host
+        seg.set_seeds(seeds)
+        t0 = time.perf_counter()
+        info0 = seg.setup()
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = seg.step(nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        nvox = n1 * n2 * n3 * n4
+        sweeps = info["sweeps_total"]
+        peak, peak_kind = _peaks()
+        rate = nvox * sweeps / (info["sweep_ms"] / 1000.0)
+        return {"workload": f"567x577x147x70 ({nvox} voxels, {count} nuclei), {nsteps} steps, "
+                            f"lean handle", "voxels": nvox,
+                "device_gb": _lib.Seg4D.device_bytes(dims, lean=True) / 1e9,
+                "value": nvox * sweeps / (ms / 1000.0), "unit": "voxel-sweeps/s",
+                "ms_per_time_step": ms / nsteps, "sweeps_per_time_step": sweeps / nsteps,
+                "sweep_rate": rate,
+                "roofline_frac": ALG_BYTES_PER_VOXEL_SWEEP * rate / 1e9 / peak,
+                "peak_kind": peak_kind, "last_res_rel": info["res_rel"],
+                "u_range": [info["umin"], info["umax"]], "setup_s": t_setup,
+                "setup_sweeps": info0["sweeps_total"], "generate_s": t_gen, "clocks": clocks,
+                "data": "synthetic, generated on the device frame by frame (seeded)"}
+    finally:
+        seg.close()
+        torch.cuda.empty_cache()
+
+
 def run_batched(nwin, nsteps, params, plain_sample=48):
     """Per-nucleus windows (edge U[24,64], 8-16 frames) advanced by the batch
     engine in mixed precision (BF16 sweep weights, FP32 defect passes) with
@@ -391,6 +448,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="arrival horizon of the serving measurement (0 = skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--paper-steps", type=int, default=0,
+                    help="time steps of the 567x577x147x70 grid with a lean handle (0 = skip)")
     ap.add_argument("--mixed-steps", type=int, default=2,
                     help="segmentations of the mixed-precision measurement (0 = skip)")
     ap.add_argument("--large-steps", type=int, default=20,
@@ -528,9 +587,11 @@ def main():
     seg.close()
     del img_d
     torch.cuda.empty_cache()
-    batched = serving = large = None
+    batched = serving = large = paper = None
     if args.large_steps > 0:
         large = run_large(args.large_steps, params, local)
+    if args.paper_steps > 0:
+        paper = run_paper_scale(args.paper_steps, params, local)
     if args.batched_windows > 0:
         batched = run_batched(args.batched_windows, args.batched_steps, params)
     if args.serve_seconds > 0:
@@ -562,6 +623,7 @@ def main():
             "clocks": clocks,
             "mixed_precision": mixed,
             "large": large,
+            "paper_scale": paper,
             "batched": batched,
             "serving": serving,
         }

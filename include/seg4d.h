@@ -145,6 +145,19 @@ void seg4d_default_params(seg4d_params *p);
  * Errors: INVALID (sizes), OOM, CUDA. */
 seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out);
 
+/* seg4d_create with flags.  SEG4D_CREATE_LEAN: 80 instead of 120 bytes per
+ * voxel, for the largest grids (the paper's 567x577x147x70 zebrafish stack,
+ * Section 4, needs 269 GB this way).  The image fields are kept inside the
+ * G array until the set-up has used them (they cannot be read back after
+ * it, and new seeds need set_image again; u serves as scratch during the
+ * set-up, which therefore re-initialises it from the seeds); the FP32 solve
+ * sweeps its
+ * correction system unscaled (c/D streamed instead of stored scaled
+ * weights: about 8 % slower per sweep).  Errors as seg4d_create, and INVALID
+ * for unknown flags. */
+enum { SEG4D_CREATE_LEAN = 1 };
+seg4d_status seg4d_create_ex(const seg4d_dims *dims, void *cuda_stream, int flags, seg4d **out);
+
 /* Free the handle and its device memory.  NULL is accepted. */
 seg4d_status seg4d_destroy(seg4d *h);
 
@@ -211,8 +224,11 @@ seg4d_status seg4d_read_u(seg4d *h, float *dst, size_t n, int on_device);
  * CUDA. */
 seg4d_status seg4d_read_field(seg4d *h, int field, float *dst, size_t n, int on_device);
 
-/* Bytes of device memory a handle of these sizes allocates. */
+/* Bytes of device memory a handle of these sizes allocates (_ex: with the
+ * creation flags).  Mixed precision adds 12 bytes per voxel at its first
+ * solve. */
 size_t seg4d_device_bytes(const seg4d_dims *dims);
+size_t seg4d_device_bytes_ex(const seg4d_dims *dims, int flags);
 
 /* Message of the last error on this handle ("" if none); valid until the next
  * call on the handle.  h == NULL gives the message of the last failed

@@ -23,6 +23,7 @@ OK, ERR_INVALID, ERR_OOM, ERR_STATE, ERR_NOT_CONVERGED, ERR_CUDA, ERR_TIMEOUT = 
 STATUS_NAMES = {0: "OK", -1: "INVALID", -2: "OOM", -3: "STATE", -4: "NOT_CONVERGED", -5: "CUDA",
                 -6: "TIMEOUT"}
 
+CREATE_LEAN = 1   # seg4d_create_ex flag (seg4d.h)
 FIELDS = {"u": 0, "I0": 1, "ITH": 2, "Isig0": 3, "IsigTH": 4, "G": 5, "owner": 6, "diag": 7,
           "off": 8}
 FACE_FIELDS = {"G", "off"}
@@ -69,6 +70,8 @@ _P = C.c_void_p
 SIGNATURES = {
     "seg4d_default_params": (None, [C.POINTER(CParams)]),
     "seg4d_create": (C.c_int, [C.POINTER(CDims), _P, C.POINTER(_P)]),
+    "seg4d_create_ex": (C.c_int, [C.POINTER(CDims), _P, C.c_int, C.POINTER(_P)]),
+    "seg4d_device_bytes_ex": (C.c_size_t, [C.POINTER(CDims), C.c_int]),
     "seg4d_destroy": (C.c_int, [_P]),
     "seg4d_set_params": (C.c_int, [_P, C.POINTER(CParams)]),
     "seg4d_set_image": (C.c_int, [_P, _P, C.c_size_t, C.c_int]),
@@ -190,7 +193,7 @@ class Seg4D:
     dims = (n1, n2, n3, n4) with n1 the fastest (x) axis and n4 the frames;
     arrays are shaped (n4, n3, n2, n1)."""
 
-    def __init__(self, dims, stream=None, params: Params | None = None):
+    def __init__(self, dims, stream=None, params: Params | None = None, lean: bool = False):
         self.lib = load()
         self.dims = tuple(int(x) for x in dims)
         n1, n2, n3, n4 = self.dims
@@ -200,7 +203,8 @@ class Seg4D:
         h = C.c_void_p()
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream
-        st = self.lib.seg4d_create(C.byref(cd), C.c_void_p(stream or 0), C.byref(h))
+        st = self.lib.seg4d_create_ex(C.byref(cd), C.c_void_p(stream or 0),
+                                      CREATE_LEAN if lean else 0, C.byref(h))
         if st != OK:
             raise Seg4DError(st, self.lib.seg4d_last_error(None).decode())
         self.h = h
@@ -307,9 +311,10 @@ class Seg4D:
         return out
 
     @staticmethod
-    def device_bytes(dims) -> int:
+    def device_bytes(dims, lean: bool = False) -> int:
         n1, n2, n3, n4 = dims
-        return int(load().seg4d_device_bytes(C.byref(CDims(n1, n2, n3, n4))))
+        return int(load().seg4d_device_bytes_ex(C.byref(CDims(n1, n2, n3, n4)),
+                                                CREATE_LEAN if lean else 0))
 
 
 # ----------------------------------------------------------------- batches

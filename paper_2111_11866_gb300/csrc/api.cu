@@ -90,6 +90,8 @@ struct seg4d {
     bool need_u0 = false;
     bool has_u = false;
     bool has_coef = false;
+    bool lean = false;      // SEG4D_CREATE_LEAN: 80 B/voxel, images not kept
+    bool img_live = false;  // lean: the image planes inside G still hold the image
     std::string err;
 };
 
@@ -149,8 +151,14 @@ bool dims_ok(const seg4d_dims *d)
     return nv < (1LL << 33);
 }
 
-size_t bytes_for(const Layout &L, long long nv)
+size_t bytes_for(const Layout &L, long long nv, bool lean = false)
 {
+    if (lean) {
+        // u, beta, gamma, diag, W, G, owner, ib, rho, dlt (see seg4d_create_ex)
+        const size_t S = (size_t)L.S;
+        return 2 * S * 4 * 4 + 8 * S * 4 + 16 * S * 4 + 2 * S * 4 + 3 * 2 * S * 4 +
+               3 * kPartCap * sizeof(double) + 8 * sizeof(double);
+    }
     const size_t S = (size_t)L.S;
     size_t b = 0;
     b += 2 * S * sizeof(float) * 4;        // u, beta, gamma, diag
@@ -177,12 +185,14 @@ void free_all(seg4d *h)
     cudaFree(h->diag);
     cudaFree(h->W);
     cudaFree(h->G);
-    cudaFree(h->I0);
-    cudaFree(h->ITH);
-    cudaFree(h->Is0);
-    cudaFree(h->IsTH);
+    if (!h->lean) {
+        cudaFree(h->I0);
+        cudaFree(h->ITH);
+        cudaFree(h->Is0);
+        cudaFree(h->IsTH);
+    }
     cudaFree(h->owner);
-    cudaFree(h->stage);
+    if (!h->lean) cudaFree(h->stage);
     cudaFree(h->partials);
     cudaFree(h->scal);
     cudaFree(h->wave_ctrl);
@@ -259,7 +269,7 @@ seg4d_status ensure_solve_arrays(seg4d *h, bool mixed)
     if (ok && mixed)
         ok = alloc(&h->Wb, 4 * S2 * sizeof(unsigned short)) &&
              alloc((void **)&h->gb, S2 * sizeof(float));
-    if (ok && !mixed)
+    if (ok && !mixed && !h->lean)
         ok = alloc((void **)&h->Ws, 4 * S2 * sizeof(float)) &&
              alloc((void **)&h->rs, S2 * sizeof(float));
     if (!ok) return fail(h, SEG4D_ERR_OOM, "solve arrays: device allocation failed");
@@ -286,6 +296,9 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
     if ((st = ensure_solve_arrays(h, mixed))) return st;
     if (mixed) {
         launch_mixed_prepare(L, h->W, h->gamma, h->diag, h->Wb, h->gb, h->ib, h->stream);
+        h->launches += 1;
+    } else if (h->lean) {   // unscaled correction sweeps: ib = 1/D, no Ws / r
+        launch_plain_prepare(L, h->gamma, h->diag, nullptr, h->ib, h->stream);
         h->launches += 1;
     } else {
         launch_plain_prepare(L, h->gamma, h->diag, h->rs, h->ib, h->stream);
@@ -346,21 +359,24 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
         } else if (h->p.sweep_variant == 0) {
             CK(cudaMemsetAsync(h->wave_ctrl, 0, (4 + h->wave_T) * sizeof(unsigned), h->stream));
             const int per_sm = std::min(h->p.ctas_per_sm > 0 ? h->p.ctas_per_sm : 4, h->wave_occ);
-            launch_sweep_wave(L, n, h->dlt, h->rho, nullptr, h->Ws, (float)omega, h->wave_ctrl,
+            launch_sweep_wave(L, n, h->dlt, h->rho, h->lean ? h->gamma : nullptr,
+                              h->lean ? h->W : h->Ws, (float)omega, h->wave_ctrl,
                               per_sm * h->num_sms, h->p.wait_test, h->stream);
             h->launches += 1;
             h->sweep_launches += 1;
         } else {
+            const float *gam = h->lean ? h->gamma : nullptr;
+            const float *wts = h->lean ? h->W : h->Ws;
             for (int s = 0; s < n; ++s) {
-                launch_sweep(L, 0, h->dlt, h->rho, nullptr, h->Ws, (float)omega, h->stream);
-                launch_sweep(L, 1, h->dlt, h->rho, nullptr, h->Ws, (float)omega, h->stream);
+                launch_sweep(L, 0, h->dlt, h->rho, gam, wts, (float)omega, h->stream);
+                launch_sweep(L, 1, h->dlt, h->rho, gam, wts, (float)omega, h->stream);
             }
             h->launches += 2LL * n;
             h->sweep_launches += 2LL * n;
         }
         CK_LAUNCH("sweep");
         CK(cudaEventRecord(h->evs1, h->stream));
-        if (mixed)
+        if (mixed || h->lean)
             launch_apply(L, x, h->dlt, h->stream);
         else
             launch_apply_scaled(L, x, h->dlt, h->rs, h->stream);
@@ -462,13 +478,27 @@ seg4d_status run_setup(seg4d *h, long long &sweeps)
     const Layout &L = h->L;
     seg4d_status st;
     if (h->setup_dirty) {
+        if (h->lean && !h->img_live)
+            return fail(h, SEG4D_ERR_STATE,
+                        "a lean handle keeps no image after its set-up: call set_image again");
         if ((st = upload_seeds(h))) return st;
+        // Where the image fields live.  A lean handle keeps them inside G (not
+        // computed yet; 8 planes of 2S floats): I0 in plane 0, I^TH in plane 2,
+        // I_sigma^TH in plane 3, I_sigma^0 in u (set from the seeds at the
+        // end); the owner keys borrow W.
+        const size_t plane = 2 * (size_t)L.S;
+        float *I0 = h->I0;
+        float *ITH = h->lean ? h->G + 2 * plane : h->ITH;
+        float *Is0 = h->lean ? h->u : h->Is0;
+        float *IsTH = h->lean ? h->G + 3 * plane : h->IsTH;
         // owners of the thresholding / rescaling balls
         CK(cudaMemsetAsync(h->owner, 0x7F, 2 * L.S * sizeof(int), h->stream));
         if (h->nseeds > 0) {
             unsigned long long *dkey = nullptr;
-            if (cudaMallocAsync((void **)&dkey, 2 * L.S * sizeof(unsigned long long), h->stream) !=
-                cudaSuccess) {
+            if (h->lean) {
+                dkey = (unsigned long long *)h->W;   // 8S floats hold 2S keys
+            } else if (cudaMallocAsync((void **)&dkey, 2 * L.S * sizeof(unsigned long long),
+                                       h->stream) != cudaSuccess) {
                 cudaGetLastError();
                 return fail(h, SEG4D_ERR_OOM, "owner distance buffer: allocation failed");
             }
@@ -476,23 +506,32 @@ seg4d_status run_setup(seg4d *h, long long &sweeps)
             launch_owner(L, h->seeds_d, h->nseeds, h->p.r_ball, dkey, h->owner, h->stream);
             h->launches += 2;
             CK_LAUNCH("owner");
-            CK(cudaFreeAsync(dkey, h->stream));
+            if (h->lean)   // W's padding slots must read as zero again
+                CK(cudaMemsetAsync(h->W, 0, 8 * L.S * sizeof(float), h->stream));
+            else
+                CK(cudaFreeAsync(dkey, h->stream));
         }
         // local thresholding
-        CK(cudaMemcpyAsync(h->ITH, h->I0, 2 * L.S * sizeof(float), cudaMemcpyDeviceToDevice,
+        CK(cudaMemcpyAsync(ITH, I0, 2 * L.S * sizeof(float), cudaMemcpyDeviceToDevice,
                            h->stream));
         if (h->nseeds > 0) {
-            launch_ball_minmax(L, h->seeds_d, h->nseeds, h->p.r_ball, h->I0, h->stat_d, h->stream);
+            launch_ball_minmax(L, h->seeds_d, h->nseeds, h->p.r_ball, I0, h->stat_d, h->stream);
             launch_threshold_apply(L, h->seeds_d, h->nseeds, h->p.r_ball, h->p.lambda_th,
-                                   h->stat_d, h->owner, h->I0, h->ITH, h->stream);
+                                   h->stat_d, h->owner, I0, ITH, h->stream);
             h->launches += 2;
             CK_LAUNCH("threshold");
         }
         // presmoothing of both images, then the face coefficients
-        if ((st = presmooth(h, h->I0, h->Is0, sweeps))) return st;
-        if ((st = presmooth(h, h->ITH, h->IsTH, sweeps))) return st;
-        launch_face_G(L, h->Is0, h->IsTH, h->p.h, h->p.K, h->p.delta, h->p.vartheta, h->G,
-                      h->stream);
+        if ((st = presmooth(h, I0, Is0, sweeps))) return st;
+        if ((st = presmooth(h, ITH, IsTH, sweeps))) return st;
+        if (h->lean) {   // G overwrites plane 3: I_sigma^TH moves to the scratch first
+            CK(cudaMemcpyAsync(h->rho, IsTH, plane * sizeof(float), cudaMemcpyDeviceToDevice,
+                               h->stream));
+            IsTH = h->rho;
+            h->img_live = false;
+            h->need_u0 = true;   // u held I_sigma^0
+        }
+        launch_face_G(L, Is0, IsTH, h->p.h, h->p.K, h->p.delta, h->p.vartheta, h->G, h->stream);
         h->launches += 1;
         CK_LAUNCH("face_G");
         h->setup_dirty = false;
@@ -618,16 +657,28 @@ void seg4d_default_params(seg4d_params *p)
     p->precision = 0;
 }
 
-size_t seg4d_device_bytes(const seg4d_dims *dims)
+size_t seg4d_device_bytes(const seg4d_dims *dims) { return seg4d_device_bytes_ex(dims, 0); }
+
+size_t seg4d_device_bytes_ex(const seg4d_dims *dims, int flags)
 {
     if (!dims_ok(dims)) return 0;
     Layout L = make_layout(*dims);
-    return bytes_for(L, (long long)dims->n1 * dims->n2 * dims->n3 * dims->n4);
+    return bytes_for(L, (long long)dims->n1 * dims->n2 * dims->n3 * dims->n4,
+                     (flags & SEG4D_CREATE_LEAN) != 0);
 }
 
 seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out)
 {
+    return seg4d_create_ex(dims, cuda_stream, 0, out);
+}
+
+seg4d_status seg4d_create_ex(const seg4d_dims *dims, void *cuda_stream, int flags, seg4d **out)
+{
     g_create_error.clear();
+    if (flags & ~SEG4D_CREATE_LEAN) {
+        g_create_error = "unknown creation flags";
+        return SEG4D_ERR_INVALID;
+    }
     if (!out) {
         g_create_error = "out is NULL";
         return SEG4D_ERR_INVALID;
@@ -650,20 +701,33 @@ seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out
     const Layout &L = h->L;
     const size_t S = (size_t)L.S;
     const long long nv = nvox(h);
+    h->lean = (flags & SEG4D_CREATE_LEAN) != 0;
     struct A {
         void **p;
         size_t bytes;
-    } allocs[] = {
+    };
+    std::vector<A> allocs = {
         {(void **)&h->u, 2 * S * 4},     {(void **)&h->beta, 2 * S * 4},
         {(void **)&h->gamma, 2 * S * 4}, {(void **)&h->diag, 2 * S * 4},
         {(void **)&h->W, 8 * S * 4},     {(void **)&h->G, 16 * S * 4},
-        {(void **)&h->I0, 2 * S * 4},    {(void **)&h->ITH, 2 * S * 4},
-        {(void **)&h->Is0, 2 * S * 4},   {(void **)&h->IsTH, 2 * S * 4},
-        {(void **)&h->owner, 2 * S * 4}, {(void **)&h->stage, (size_t)nv * 4},
+        {(void **)&h->owner, 2 * S * 4},
         {(void **)&h->partials, 3 * kPartCap * sizeof(double)},
         {(void **)&h->scal, 8 * sizeof(double)},
         {(void **)&h->wave_ctrl, (4 + (size_t)wave_tiles(L)) * sizeof(unsigned)},
     };
+    if (h->lean) {
+        // the solve's scratch exists from the start; staging and the image
+        // fields live inside it and inside G (see run_setup)
+        allocs.push_back({(void **)&h->ib, 2 * S * 4});
+        allocs.push_back({(void **)&h->rho, 2 * S * 4});
+        allocs.push_back({(void **)&h->dlt, 2 * S * 4});
+    } else {
+        allocs.push_back({(void **)&h->I0, 2 * S * 4});
+        allocs.push_back({(void **)&h->ITH, 2 * S * 4});
+        allocs.push_back({(void **)&h->Is0, 2 * S * 4});
+        allocs.push_back({(void **)&h->IsTH, 2 * S * 4});
+        allocs.push_back({(void **)&h->stage, (size_t)nv * 4});
+    }
     for (auto &a : allocs) {
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -679,6 +743,10 @@ seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out
             g_create_error = "cudaMemsetAsync failed";
             return SEG4D_ERR_CUDA;
         }
+    }
+    if (h->lean) {
+        h->stage = h->rho;   // 2S >= n1 n2 n3 n4 floats
+        h->I0 = h->G;        // plane 0 of G until the set-up computes G
     }
     h->wave_T = wave_tiles(L);
     h->wave_occ = wave_max_ctas_per_sm();
@@ -754,9 +822,11 @@ seg4d_status seg4d_set_image(seg4d *h, const float *I0, size_t n, int on_device)
         for (size_t v = 0; v < n; ++v)
             if (!std::isfinite(I0[v])) return fail(h, SEG4D_ERR_INVALID, "image has NaN/Inf");
     }
+    if (h->lean) h->I0 = h->G;
     if ((st = copy_in(h, I0, n, on_device, h->I0))) return st;
     CK(cudaStreamSynchronize(h->stream));
     h->has_image = true;
+    h->img_live = true;
     h->setup_dirty = true;
     return SEG4D_OK;
 }
@@ -942,10 +1012,14 @@ seg4d_status seg4d_read_field(seg4d *h, int field, float *dst, size_t n, int on_
         return seg4d_read_u(h, dst, n, on_device);
     case SEG4D_FIELD_I0:
         if (!h->has_image) return fail(h, SEG4D_ERR_STATE, "no image set");
+        if (h->lean && !h->img_live)
+            return fail(h, SEG4D_ERR_STATE, "a lean handle keeps no image after its set-up");
         return copy_out(h, h->I0, dst, n, on_device);
     case SEG4D_FIELD_ITH:
     case SEG4D_FIELD_ISIG0:
     case SEG4D_FIELD_ISIGTH:
+        if (h->lean) return fail(h, SEG4D_ERR_STATE, "a lean handle keeps no image fields");
+        [[fallthrough]];
     case SEG4D_FIELD_OWNER:
     case SEG4D_FIELD_G:
         if (!h->has_image || h->setup_dirty)

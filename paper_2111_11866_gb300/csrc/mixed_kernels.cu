@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(256, SEG4D_DEFECT_MINB) k_defect(Layout L, con
 // Before an FP32 solve (the correction sweeps run on the scaled system, see
 // k_scaled_weights): per voxel r = sqrt(gamma) and ib = 1 / (D r), so that
 // the defect pass writes the scaled right-hand side rho = r_res / (D r).
+// Without rs (a lean handle sweeps the unscaled correction system) ib = 1/D.
 // Padding slots (gamma = 0) get r = ib = 0.
 __global__ void __launch_bounds__(256) k_plain_prepare(long long n4,
                                                        const float4 *__restrict__ gamma,
@@ -138,9 +139,10 @@ __global__ void __launch_bounds__(256) k_plain_prepare(long long n4,
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             rp[m] = gp[m] > 0.0f ? sqrtf(gp[m]) : 0.0f;
-            ip[m] = gp[m] > 0.0f ? 1.0f / (dp[m] * rp[m]) : 0.0f;
+            // unscaled correction system (no rs): rho = r_res / D
+            ip[m] = gp[m] > 0.0f ? 1.0f / (rs ? dp[m] * rp[m] : dp[m]) : 0.0f;
         }
-        rs[e] = r;
+        if (rs) rs[e] = r;
         ib[e] = iv;
     }
 }

@@ -156,15 +156,14 @@ def nuclei(seed: int, n, count: int | None = None, density_per_voxel: float | No
                 {"count": count, "semi_axes": semi, "peaks": peaks, "paths": paths})
 
 
-def nuclei_device(seed: int, n, density_per_voxel: float, device, axes=(4.0, 9.0),
+def nuclei_frames(seed: int, n, density_per_voxel: float, device, axes=(4.0, 9.0),
                   peak=(0.5, 1.0), background: float = 0.05, photons: float = 1000.0,
-                  read_noise: float = 0.05, nsteps: int = 20, margin: float = 10.0,
-                  name: str = "nuclei (device)"):
-    """The nuclei() recipe for grids too large to build on the host: the
-    per-nucleus draws (paths, semi-axes, peaks) come from the same seeded
-    numpy generator, the image and its noise are made on `device` with a
-    seeded torch generator.  Returns (image tensor (n4, n3, n2, n1) float32 on
-    the device, seeds (m, 4), nsteps, meta)."""
+                  read_noise: float = 0.05, margin: float = 10.0):
+    """The nuclei() recipe frame by frame on `device`, for grids too large to
+    build at once: the per-nucleus draws (paths, semi-axes, peaks) come from
+    the same seeded numpy generator, each frame's image and noise from a seeded
+    torch generator.  Returns (seeds (m, 4), count, generator of the n4 frames
+    as (n3, n2, n1) float32 tensors on the device, in order)."""
     import torch
 
     rng = np.random.default_rng(seed)
@@ -175,35 +174,50 @@ def nuclei_device(seed: int, n, density_per_voxel: float, device, axes=(4.0, 9.0
     paths = _trajectories(rng, count, n4, lo, hi)
     semi = rng.uniform(axes[0], axes[1], size=(count, 3))
     peaks = rng.uniform(peak[0], peak[1], size=count)
-    img = torch.full((n4, n3, n2, n1), background, dtype=torch.float32, device=device)
-    ar = [torch.arange(m, dtype=torch.float32, device=device) for m in (n1, n2, n3)]
-    for l in range(n4):
-        frame = img[l]
-        for a in range(count):
-            c = paths[a, l]
-            ext = 2.0 * semi[a]
-            x0, x1 = max(0, int(c[0] - ext[0])), min(n1, int(c[0] + ext[0]) + 2)
-            y0, y1 = max(0, int(c[1] - ext[1])), min(n2, int(c[1] + ext[1]) + 2)
-            z0, z1 = max(0, int(c[2] - ext[2])), min(n3, int(c[2] + ext[2]) + 2)
-            if x0 >= x1 or y0 >= y1 or z0 >= z1:
-                continue
-            rx = ((ar[0][x0:x1] - float(c[0])) / float(semi[a, 0])) ** 2
-            ry = ((ar[1][y0:y1] - float(c[1])) / float(semi[a, 1])) ** 2
-            rz = ((ar[2][z0:z1] - float(c[2])) / float(semi[a, 2])) ** 2
-            r2 = rz[:, None, None] + ry[None, :, None] + rx[None, None, :]
-            sub = frame[z0:z1, y0:y1, x0:x1]
-            torch.maximum(sub, float(peaks[a]) * torch.exp(-2.0 * r2), out=sub)
-    g = torch.Generator(device=device)
-    g.manual_seed(seed)
-    for l in range(n4):   # noise frame by frame: bounded temporaries
-        f = img[l]
-        f.copy_(torch.poisson(f.clamp_(min=0.0) * photons, generator=g) / photons +
-                read_noise * torch.randn(f.shape, generator=g, device=device))
     cen = np.rint(paths[:, 0, :])
     cen[:, 0] = np.clip(cen[:, 0], 0, n1 - 1)
     cen[:, 1] = np.clip(cen[:, 1], 0, n2 - 1)
     cen[:, 2] = np.clip(cen[:, 2], 0, n3 - 1)
     seeds = np.concatenate([cen, np.zeros((count, 1))], axis=1)
+
+    def frames():
+        ar = [torch.arange(m, dtype=torch.float32, device=device) for m in (n1, n2, n3)]
+        g = torch.Generator(device=device)
+        g.manual_seed(seed)
+        for l in range(n4):
+            frame = torch.full((n3, n2, n1), background, dtype=torch.float32, device=device)
+            for a in range(count):
+                c = paths[a, l]
+                ext = 2.0 * semi[a]
+                x0, x1 = max(0, int(c[0] - ext[0])), min(n1, int(c[0] + ext[0]) + 2)
+                y0, y1 = max(0, int(c[1] - ext[1])), min(n2, int(c[1] + ext[1]) + 2)
+                z0, z1 = max(0, int(c[2] - ext[2])), min(n3, int(c[2] + ext[2]) + 2)
+                if x0 >= x1 or y0 >= y1 or z0 >= z1:
+                    continue
+                rx = ((ar[0][x0:x1] - float(c[0])) / float(semi[a, 0])) ** 2
+                ry = ((ar[1][y0:y1] - float(c[1])) / float(semi[a, 1])) ** 2
+                rz = ((ar[2][z0:z1] - float(c[2])) / float(semi[a, 2])) ** 2
+                r2 = rz[:, None, None] + ry[None, :, None] + rx[None, None, :]
+                sub = frame[z0:z1, y0:y1, x0:x1]
+                torch.maximum(sub, float(peaks[a]) * torch.exp(-2.0 * r2), out=sub)
+            frame.copy_(torch.poisson(frame.clamp_(min=0.0) * photons, generator=g) / photons +
+                        read_noise * torch.randn(frame.shape, generator=g, device=device))
+            yield frame
+
+    return seeds, count, frames()
+
+
+def nuclei_device(seed: int, n, density_per_voxel: float, device, nsteps: int = 20,
+                  name: str = "nuclei (device)", **kw):
+    """nuclei_frames assembled into one (n4, n3, n2, n1) tensor on the device.
+    Returns (image, seeds (m, 4), nsteps, meta)."""
+    import torch
+
+    seeds, count, frames = nuclei_frames(seed, n, density_per_voxel, device, **kw)
+    n1, n2, n3, n4 = n
+    img = torch.empty((n4, n3, n2, n1), dtype=torch.float32, device=device)
+    for l, f in enumerate(frames):
+        img[l].copy_(f)
     return img, seeds, nsteps, {"count": count, "name": name}
 
 
@@ -212,6 +226,16 @@ def large(device, seed: int = 3):
     voxels (about 524), 20 steps; built on the device (nuclei_device)."""
     return nuclei_device(seed, (512, 512, 128, 48), 1.0 / 40 ** 3, device, nsteps=20,
                          name="large 512x512x128x48, 1 nucleus per 40^3")
+
+
+def paper_scale(device, seed: int = 7):
+    """The size of the paper's largest stack (567x577x147 x 70 frames,
+    3,366,466,110 voxels; Section 4, the zebrafish pectoral fin), with the
+    nucleus generator at one nucleus per 40^3 voxels.  Returns
+    (dims, seeds, count, frame generator) as nuclei_frames."""
+    n = (567, 577, 147, 70)
+    seeds, count, frames = nuclei_frames(seed, n, 1.0 / 40 ** 3, device)
+    return n, seeds, count, frames
 
 
 def medium(seed: int = 2) -> Case:
