@@ -86,10 +86,13 @@ typedef struct {
                            pass r = b - A u; the sweeps solve A_b delta = r and
                            u += delta, so the fixed point is the FP32 system's.
                            Presmoothing solves are always FP32.                    */
-    int sweep_variant;  /* 0 = fused red-black wavefront (one pass per sweep),
-                           1 = one launch per colour (default); both give
-                           identical bits                                          */
-    int ctas_per_sm;    /* resident CTAs per SM of the fused sweep (0 = default 4)  */
+    int sweep_variant;  /* 0 = fused frame pipeline: one persistent launch per
+                           batch of sweeps, red of frame s and black of frame
+                           s-2 together, face weights re-read from L2;
+                           1 = one launch per colour (default, faster on the
+                           measured grids); both give identical bits         */
+    int ctas_per_sm;    /* resident CTAs per SM of the fused sweep (0 = as many
+                           as fit, at most 4)                                    */
     int wait_test;      /* test hook, 0 normally.  1: the first work item of the
                            fused sweep also waits for a flag that nothing sets,
                            so its bounded wait expires (about 2 s) and the call

@@ -255,15 +255,17 @@ def test_device_pointers_roundtrip():
 # ---------------------------------------------------------------- fused sweep
 
 SWEEP_DIMS = [(69, 21, 13, 5), (40, 17, 6, 1), (31, 9, 5, 2), (64, 24, 12, 7), (3, 2, 1, 4),
-              (201, 7, 5, 3), (130, 9, 4, 2)]
+              (201, 7, 5, 3), (130, 9, 4, 2), (1100, 5, 3, 2)]
 
 
 @pytest.mark.parametrize("dims", SWEEP_DIMS)
-def test_sweep_variants_bit_identical(dims):
-    """The wavefront sweep (0, one voxel per thread) performs exactly the
-    red-then-black sweeps of the per-colour launches (1, two voxels per
-    thread): same iterates bit for bit, same sweep counts (ragged rows and
-    tiles, rows longer than one warp's 64 slots, n4 = 1 and 2)."""
+@pytest.mark.parametrize("lean", [False, True])
+def test_sweep_variants_bit_identical(dims, lean):
+    """The fused frame pipeline (0) performs exactly the red-then-black sweeps
+    of the per-colour launches (1): same iterates bit for bit, same sweep
+    counts (ragged rows and tiles, rows of one to nine warps' 64 slots, so
+    that a tile holds up to 12 row-chunks, n4 = 1 and 2), on the scaled
+    system of the full handle and the unscaled one of the lean handle."""
     n1, n2, n3, n4 = dims
     image = synth.random_field(sum(dims), dims)
     seeds = [(n1 // 2, n2 // 2, n3 // 2, 0), (n1 // 3, n2 // 3, n3 // 3, n4 - 1)]
@@ -272,7 +274,7 @@ def test_sweep_variants_bit_identical(dims):
         p = _lib.Params.defaults()
         p.r_ball = p.R_init = 5.0
         p.sweep_variant = variant
-        with _lib.Seg4D(dims, params=p) as s:
+        with _lib.Seg4D(dims, params=p, lean=lean) as s:
             s.set_image(image)
             s.set_seeds(seeds)
             info = s.step(2)
