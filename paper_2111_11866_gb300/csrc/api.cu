@@ -135,6 +135,8 @@ Layout make_layout(const seg4d_dims &d)
     L.njb = (d.n2 + 7) / 8;
     L.R = d.n2 * d.n3 * d.n4;
     L.S = (long long)L.R * L.P;
+    L.kt = plane_tile(d.n2, d.n3, d.n4, L.P);
+    L.ntile = (d.n3 + L.kt - 1) / L.kt;
     return L;
 }
 
@@ -144,9 +146,14 @@ bool dims_ok(const seg4d_dims *d)
     if (d->n3 > 65535 || d->n4 > 65535) return false;   // grid.y / grid.z of the sweep
     const long long rows = (long long)d->n2 * d->n3 * d->n4;
     if (rows >= (1LL << 31)) return false;
-    // work items of the tile loops (2 colours x 32-slot chunks x 8-row blocks)
-    const long long chunks = ((d->n1 + 1) / 2 + 3) / 4 * 4 / 32 + 1;
-    if (2 * chunks * ((d->n2 + 7) / 8) * d->n3 * d->n4 >= (1LL << 31)) return false;
+    // work items of the tile loops (2 colours x 32-slot chunks x 8-row blocks
+    // x the planes of the traversal order, holes of the last z-tile included)
+    const int P = ((d->n1 + 1) / 2 + 3) / 4 * 4;
+    const long long chunks = P / 32 + 1;
+    const int kt = plane_tile(d->n2, d->n3, d->n4, P);
+    const long long planes = (long long)((d->n3 + kt - 1) / kt) * kt * d->n4;
+    if ((d->n3 + kt - 1) / kt * (long long)d->n4 > 65535) return false;
+    if (2 * chunks * ((d->n2 + 7) / 8) * planes >= (1LL << 31)) return false;
     const long long nv = rows * d->n1;
     return nv < (1LL << 33);
 }

@@ -585,6 +585,8 @@ Layout layout_of(const seg4d_dims &d)
     L.njb = (d.n2 + 7) / 8;
     L.R = d.n2 * d.n3 * d.n4;
     L.S = (long long)L.R * L.P;
+    L.kt = L.n3;
+    L.ntile = 1;
     return L;
 }
 

@@ -35,7 +35,30 @@ struct Layout {
     int njb;        // ceil(n2 / 8): 8-row blocks along y
     int R;          // rows = n2*n3*n4
     long long S;    // slots per colour = R*P
+    int kt;         // z-planes per tile of the plane traversal order
+    int ntile;      // ceil(n3 / kt)
 };
+
+// Traversal order of the (k, l) planes in the stencil kernels: tiles of kt
+// consecutive z-planes, l-major inside a tile (plane index c = tile n4 + l,
+// then k = tile kt + kin, kin fastest), so that the t-neighbour planes of a
+// plane are visited kt planes apart rather than n3 apart.  With kt chosen so
+// that 2 kt planes of sweep traffic stay well inside L2, values read through
+// the +-t faces are L2 hits on large grids too.  kt = n3 is the plain order
+// (k fastest, then l).  Plane slots with k >= n3 (the last tile) are holes.
+//
+// kt for a grid: about 64 MB of sweep traffic (48 B per slot and colour)
+// over 2 kt planes; grids whose frame-to-frame distance already fits keep
+// kt = n3.  ntile n4 stays within a grid dimension (65535).
+inline int plane_tile(int n2, int n3, int n4, int P)
+{
+    const double plane = 96.0 * (double)n2 * (double)P;
+    int kt = (int)(64.0e6 / plane);
+    if (kt < 1) kt = 1;
+    if (2 * kt >= n3) kt = n3;
+    while (kt < n3 && (long long)((n3 + kt - 1) / kt) * n4 > 65535) ++kt;
+    return kt;
+}
 
 // Voxel coordinates -> colour and slot (caller guarantees the voxel exists).
 __host__ __device__ inline long long slot_of(const Layout &L, int i, int j, int k, int l,

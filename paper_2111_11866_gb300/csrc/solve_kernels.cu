@@ -10,30 +10,6 @@
 
 namespace seg4d_impl {
 
-// Grid-stride loop over the sweep's tiles (32 slots x 8 rows along y at one
-// (k, l)); a block of 256 threads takes one tile per iteration, lane -> slot,
-// warp -> row, so each iteration issues the same coalesced loads as a sweep.
-#define FOR_TILES(L, s, rp, row, BODY)                                                     \
-    {                                                                                      \
-        const long long ntile_ = (long long)(L).nchunk * (L).njb * (L).n3 * (L).n4;       \
-        for (long long t_ = blockIdx.x; t_ < ntile_; t_ += gridDim.x) {                    \
-            const int chunk_ = (int)(t_ % (L).nchunk);                                     \
-            long long r_ = t_ / (L).nchunk;                                                \
-            const int jb_ = (int)(r_ % (L).njb);                                           \
-            r_ /= (L).njb;                                                                 \
-            RowPos rp;                                                                     \
-            rp.k = (int)(r_ % (L).n3);                                                     \
-            rp.l = (int)(r_ / (L).n3);                                                     \
-            rp.j = jb_ * 8 + (int)(threadIdx.x >> 5);                                      \
-            const int s = chunk_ * 32 + (int)(threadIdx.x & 31);                           \
-            if (rp.j < (L).n2 && s < (L).P) {                                              \
-                rp.p = (rp.j + rp.k + rp.l) & 1;                                           \
-                const int row = rp.j + (L).n2 * (rp.k + (L).n3 * rp.l);                   \
-                BODY                                                                       \
-            }                                                                              \
-        }                                                                                  \
-    }
-
 // ------------------------------------------------------------ red-black sweep
 
 // One half sweep of colour C: every voxel of that colour gets
@@ -41,14 +17,15 @@ namespace seg4d_impl {
 //   here = beta + gamma * sum_f w_f u_nb with beta = b/D, gamma = c/D), then
 //   u <- u + omega (ubar - u)           (Eq. 5.33).
 // N voxels per thread (relax_vec): a warp covers 32 N consecutive slots of
-// one row, a block (32, 8) 8 rows; grid (row chunks x y-blocks, n3, n4).  The
-// black pass walks the grid backwards, so it starts on the data the red pass
-// touched last, which is still in L2.  The same kernel with BF16 weights
+// one row, a block (32, 8) 8 rows; grid (row chunks x y-blocks, kt,
+// ntile n4): the (k, l) planes in the tiled traversal order of Layout::kt.
+// The black pass walks that order backwards, so it starts on the data the
+// red pass touched last, which is still in L2.  The same kernel with BF16 weights
 // sweeps the correction system of the mixed-precision solve.
 template <int C, typename WT, int N, bool kUnit>
 __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_sweep_vec(
-    Layout L, float *__restrict__ x, const float *__restrict__ B, const float *__restrict__ Gm,
-    const WT *__restrict__ W, float omega)
+    Layout L, FastDiv fn4, float *__restrict__ x, const float *__restrict__ B,
+    const float *__restrict__ Gm, const WT *__restrict__ W, float omega)
 {
     const int nch = (L.P + 32 * N - 1) / (32 * N);
     const int bx = C ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
@@ -56,9 +33,12 @@ __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_sweep_vec(
     const int jb = bx / nch;
     RowPos rp;
     rp.j = jb * 8 + threadIdx.y;
-    rp.k = C ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
-    rp.l = C ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
-    if (rp.j >= L.n2) return;   // the whole warp
+    const unsigned kin = C ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+    const unsigned c = C ? gridDim.z - 1 - blockIdx.z : blockIdx.z;   // tile n4 + l
+    const unsigned tile = fdiv(c, fn4);
+    rp.k = (int)(tile * (unsigned)L.kt + kin);
+    rp.l = (int)(c - tile * (unsigned)L.n4);
+    if (rp.j >= L.n2 || rp.k >= L.n3) return;   // the whole warp
     rp.p = (rp.j + rp.k + rp.l) & 1;
     const int s0 = chunk * 32 * N + N * threadIdx.x;
     const bool act = s0 < L.P && 2 * s0 + (C ^ rp.p) < L.n1;
@@ -71,12 +51,13 @@ void launch_vec(const Layout &L, int colour, float *x, const float *B, const flo
                 const WT *W, float omega, cudaStream_t st)
 {
     dim3 block(32, 8);
-    dim3 grid((unsigned)(((L.P + 32 * N - 1) / (32 * N)) * L.njb), (unsigned)L.n3,
-              (unsigned)L.n4);
+    dim3 grid((unsigned)(((L.P + 32 * N - 1) / (32 * N)) * L.njb), (unsigned)L.kt,
+              (unsigned)(L.ntile * L.n4));
+    const FastDiv fn4 = make_fastdiv((unsigned)L.n4);
     if (colour == 0)
-        k_sweep_vec<0, WT, N, kUnit><<<grid, block, 0, st>>>(L, x, B, Gm, W, omega);
+        k_sweep_vec<0, WT, N, kUnit><<<grid, block, 0, st>>>(L, fn4, x, B, Gm, W, omega);
     else
-        k_sweep_vec<1, WT, N, kUnit><<<grid, block, 0, st>>>(L, x, B, Gm, W, omega);
+        k_sweep_vec<1, WT, N, kUnit><<<grid, block, 0, st>>>(L, fn4, x, B, Gm, W, omega);
 }
 
 void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,

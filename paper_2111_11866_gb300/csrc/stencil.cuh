@@ -83,25 +83,27 @@ __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f)
 }
 
 // Work items t = 2 * tile + colour of the tile loops: tile = (chunk, y-block
-// of 8 rows, k, l), chunk fastest, with nch chunks per row; the number of
-// items is below 2^31 (checked when the handle is created).
+// of 8 rows, plane), chunk fastest, with nch chunks per row and the planes in
+// the tiled traversal order (Layout::kt); the number of items is below 2^31
+// (checked when the handle is created).
 struct ItemDecode {
-    FastDiv fch, fjb, fn3;
+    FastDiv fch, fjb, fkt, fn4;
     unsigned nch;
 };
 
 inline ItemDecode make_item_decode(const Layout &L, int nch)
 {
     return ItemDecode{make_fastdiv((unsigned)nch), make_fastdiv((unsigned)L.njb),
-                      make_fastdiv((unsigned)L.n3), (unsigned)nch};
+                      make_fastdiv((unsigned)L.kt), make_fastdiv((unsigned)L.n4), (unsigned)nch};
 }
 
 inline long long item_count(const Layout &L, int nch)
 {
-    return 2LL * nch * L.njb * L.n3 * L.n4;
+    return 2LL * nch * L.njb * ((long long)L.ntile * L.kt) * L.n4;
 }
 
-// item t -> colour, chunk and the row position of warp `warp` (rp.p set)
+// item t -> colour, chunk and the row position of warp `warp` (rp.p set); a
+// hole of the last z-tile, like a row past n2, comes back as rp.j >= n2
 __device__ __forceinline__ void decode_item(const ItemDecode &D, const Layout &L, unsigned t,
                                             int warp, int &C, int &chunk, RowPos &rp)
 {
@@ -111,10 +113,11 @@ __device__ __forceinline__ void decode_item(const ItemDecode &D, const Layout &L
     chunk = (int)(r - a * D.nch);
     const unsigned b = fdiv(a, D.fjb);
     const int jb = (int)(a - b * (unsigned)L.njb);
-    const unsigned c = fdiv(b, D.fn3);
-    rp.k = (int)(b - c * (unsigned)L.n3);
-    rp.l = (int)c;
-    rp.j = jb * 8 + warp;
+    const unsigned c = fdiv(b, D.fkt);
+    const unsigned tile = fdiv(c, D.fn4);
+    rp.k = (int)(tile * (unsigned)L.kt + (b - c * (unsigned)L.kt));
+    rp.l = (int)(c - tile * (unsigned)L.n4);
+    rp.j = rp.k < L.n3 ? jb * 8 + warp : L.n2;
     rp.p = (rp.j + rp.k + rp.l) & 1;
 }
 
