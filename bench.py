@@ -35,9 +35,9 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per full sweep of the medium grid, from one ncu
 # capture of the current kernel (profiles/); None after a kernel changes until
 # it is captured again.
-SWEEP_KERNELS = {0: "k_sweep_wave (fused red-black wavefront, several sweeps per launch)",
+SWEEP_KERNELS = {0: "k_sweep_wave (fused frame pipeline, several sweeps per launch)",
                  1: "k_sweep_vec (one colour of a red-black sweep per launch, 2 voxels/thread)"}
-SWEEP_TRAFFIC_PER_SWEEP = {0: None, 1: 793.4e6 + 791.5e6}
+SWEEP_TRAFFIC_PER_SWEEP = {0: 10473659904 / 8, 1: 792270848 + 792436992}
 
 
 def _env_int(name, default):
@@ -221,7 +221,7 @@ def _mixed(params):
     return pm
 
 
-def run_large(nsteps, params, local):
+def run_large(nsteps, params, local, frames=48):
     """The large full grid (512x512x128 x 48 frames, 1.61G voxels, one nucleus
     per 40^3 voxels), built on the device, `nsteps` time steps after the
     set-up; whole-step voxel-sweeps/s, the sweep kernel's rate and its
@@ -229,7 +229,7 @@ def run_large(nsteps, params, local):
     import torch
     from paper_2111_11866_gb300 import _lib, synth
 
-    img, seeds, _, meta = synth.large("cuda")
+    img, seeds, _, meta = synth.large("cuda", frames=frames)
     dims = tuple(reversed(img.shape))
     nvox = img.numel()
     torch.cuda.synchronize()
@@ -454,8 +454,10 @@ def main():
                     help="segmentations of the mixed-precision measurement (0 = skip)")
     ap.add_argument("--large-steps", type=int, default=20,
                     help="time steps of the large 512x512x128x48 grid (0 = skip)")
+    ap.add_argument("--large-frames", type=int, default=48,
+                    help="frames of the large grid (fewer: the same planes, for profiling)")
     ap.add_argument("--sweep-variant", type=int, default=1, choices=[0, 1],
-                    help="0 = fused red-black wavefront sweep, 1 = one launch per colour")
+                    help="0 = fused frame-pipeline sweep, 1 = one launch per colour")
     ap.add_argument("--time-steps", type=int, default=None,
                     help="override the workload's 50 time steps (profiling runs only)")
     args = ap.parse_args()
@@ -589,7 +591,7 @@ def main():
     torch.cuda.empty_cache()
     batched = serving = large = paper = None
     if args.large_steps > 0:
-        large = run_large(args.large_steps, params, local)
+        large = run_large(args.large_steps, params, local, frames=args.large_frames)
     if args.paper_steps > 0:
         paper = run_paper_scale(args.paper_steps, params, local)
     if args.batched_windows > 0:

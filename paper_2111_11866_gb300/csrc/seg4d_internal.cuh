@@ -209,9 +209,14 @@ std::string &handle_free_error();
 // reduction kernels use; the scratch array holds 3 * kPartBlocks doubles.
 constexpr int kPartBlocks = 1024;
 constexpr int kPartThreads = 256;
-// blocks (records) of the residual kernel; the scratch array holds
+// blocks (records) of the item loops of the coefficient, defect and scaling
+// kernels: 2048 was the fastest of 912 ... 65536 in whole medium time steps
+// (more blocks cost more than their tail saves); the scratch array holds
 // 3 * max(kPartBlocks, kResBlocks) doubles
-constexpr int kResBlocks = 16384;
+#ifndef SEG4D_RES_BLOCKS
+#define SEG4D_RES_BLOCKS 2048
+#endif
+constexpr int kResBlocks = SEG4D_RES_BLOCKS;
 constexpr int kPartCap = kResBlocks > kPartBlocks ? kResBlocks : kPartBlocks;
 
 }  // namespace seg4d_impl
