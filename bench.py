@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 # it is captured again.
 SWEEP_KERNELS = {0: "k_sweep_wave (fused frame pipeline, several sweeps per launch)",
                  1: "k_sweep_vec (one colour of a red-black sweep per launch, 2 voxels/thread)"}
-SWEEP_TRAFFIC_PER_SWEEP = {0: 10473659904 / 8, 1: 792270848 + 792436992}
+SWEEP_TRAFFIC_PER_SWEEP = {0: (12189379840 + 1330637312) / 10, 1: (731106816 + 61575168) + (731059968 + 61712640)}
 
 
 def _env_int(name, default):
