@@ -2,8 +2,8 @@
 // system held entirely in the caller's device memory, computed without any
 // device allocation.
 //
-// It is a variant of the residual reduction used by every solve (k_residual +
-// k_reduce in solve_kernels.cu): per-block FP64 records followed by one
+// It follows the stopping test of every solve (k_defect in mixed_kernels.cu
+// + k_reduce in solve_kernels.cu): per-block records followed by one
 // fixed-order final reduction.  Here the per-block records live in the
 // file-scope device array below instead of memory allocated by a handle, and
 // the inputs are the caller's x-fastest arrays (u, b, diagonal and the 8

@@ -76,7 +76,7 @@ void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *
                                                (const __nv_bfloat16 *)Wb, omega, st);
 }
 
-// ------------------------------------------ fused red-black wavefront sweep
+// ------------------------------------------ fused red-black frame pipeline
 
 // One launch performs `nsweeps` complete red-black sweeps as a pipeline over
 // the frame axis l, so that on grids whose frames are small against L2 the
