@@ -141,9 +141,10 @@ def _crop_case(case, n=(64, 64, 32, 8)):
     return img, s[keep]
 
 
-def oracle_sample(case, params, nsteps=1):
+def oracle_sample(case, params, nsteps=1, omp=False):
     """The FP64 oracle, as it stands, on a crop of the workload: returns
-    (voxel-sweeps per second, description)."""
+    (voxel-sweeps per second, description, seconds).  omp: its OpenMP build
+    (the paper's frame-split red-black sweeps on all host cores)."""
     import numpy as np
     import oracle as O
     img, seeds = _crop_case(case)
@@ -152,14 +153,16 @@ def oracle_sample(case, params, nsteps=1):
                        r_ball=params.r_ball, R_init=params.R_init, v_init=params.v_init,
                        sigma_t=params.sigma_t, tol=1e-12)
     t0 = time.perf_counter()
-    u, info = O.segment(img.astype(np.float64), seeds, P, nsteps=nsteps)
+    u, info = O.segment(img.astype(np.float64), seeds, P, nsteps=nsteps, omp=omp)
     dt = time.perf_counter() - t0
     nv = img.size
     sweeps = sum(info["iters"])
-    desc = (f"oracle (plain C, FP64, 1 thread) full pipeline on a {img.shape[3]}x{img.shape[2]}x"
+    how = (f"OpenMP build, {O.threads(True)} threads, frame-split red-black sweeps" if omp
+           else "1 thread")
+    desc = (f"oracle (plain C, FP64, {how}) full pipeline on a {img.shape[3]}x{img.shape[2]}x"
             f"{img.shape[1]}x{img.shape[0]} crop of the workload ({len(seeds)} seeds), {nsteps} "
             f"step(s) solved to 1e-12; counts step-solve sweeps, times set-up too")
-    return nv * sweeps / dt, desc, dt
+    return nv * sweeps / dt, desc, dt, (O.threads(True) if omp else 1)
 
 
 def run_reference(args, rank, world):
@@ -176,7 +179,7 @@ def run_reference(args, rank, world):
     vals, times = [], []
     desc = ""
     for _ in range(args.steps):
-        v, desc, dt = oracle_sample(case, params)
+        v, desc, dt, _ = oracle_sample(case, params)
         vals.append(v)
         times.append(dt)
     value = statistics.mean(vals)
@@ -581,10 +584,16 @@ def main():
                                               max(np.abs(u_plain).max(), 1e-30)),
                  "dtype": "bf16 sweep weights, f32 sweeps and defect passes, f64 norms"}
 
-    cpu = None
+    cpu = cpu_omp = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, _ = oracle_sample(case, params)
+        v, desc, _, _ = oracle_sample(case, params)
         cpu = {"value": v, "unit": "voxel-sweeps/s", "cores": 1, "kind": "oracle", "sample": desc}
+        try:
+            v, desc, _, cores = oracle_sample(case, params, omp=True)
+            cpu_omp = {"value": v, "unit": "voxel-sweeps/s", "cores": cores,
+                       "kind": "oracle, OpenMP build", "sample": desc}
+        except Exception as e:   # noqa: BLE001 -- no OpenMP toolchain on the host
+            cpu_omp = {"unavailable": f"OpenMP build of the oracle failed: {e}"[:200]}
 
     seg.close()
     del img_d
@@ -619,6 +628,7 @@ def main():
                          "sweeps_per_launch": sweeps_per_launch,
                          "avg_launch_ms": launch_ms},
             "cpu_baseline": cpu,
+            "cpu_baseline_omp": cpu_omp,
             "e2e": {"value": e2e_value, "unit": "voxel-sweeps/s",
                     "h2d_bytes_per_step": img_h.nbytes, "d2h_bytes_per_step": out_h.nbytes},
             "gpu_launches": launches,

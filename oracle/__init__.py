@@ -25,23 +25,30 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "seg4d_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libseg4d_oracle.so")
+_LIB_OMP = os.path.join(_BUILD, "libseg4d_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 OR_OK = 0
 OR_NOT_CONVERGED = 1
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (a few seconds, gcc only)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle shared library (a few seconds, gcc only).  omp: the
+    separate OpenMP build whose sweeps follow the paper's frame-split
+    red-black scheme -- a timed CPU baseline only; the tests use the plain
+    build."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+    out = _LIB_OMP if omp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
                "-std=c99", "-Wall", "-o", tmp, _SRC, "-lm"]
+        if omp:
+            cmd[1:1] = ["-fopenmp", "-DSEG4D_ORACLE_OMP"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
 class Params(C.Structure):
@@ -86,11 +93,10 @@ class OracleParams:
         return p
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if omp not in _libs:
+            L = C.CDLL(build(omp=omp))
             D = C.POINTER(C.c_double)
             I = C.POINTER(C.c_int)
             sig = {
@@ -113,8 +119,15 @@ def lib():
                 fn = getattr(L, name)
                 fn.argtypes = args
                 fn.restype = C.c_int
-            _lib = L
-    return _lib
+            L.or_threads.argtypes = []
+            L.or_threads.restype = C.c_int
+            _libs[omp] = L
+    return _libs[omp]
+
+
+def threads(omp: bool = False) -> int:
+    """Threads the sweeps of that build use."""
+    return int(lib(omp).or_threads())
 
 
 # --------------------------------------------------------------------------
@@ -249,8 +262,10 @@ def residual(diag, off, b, u) -> np.ndarray:
     return r
 
 
-def segment(I0, seeds, params: OracleParams | None = None, nsteps: int = 10):
-    """The whole pipeline; returns (u, info) with per-step sweeps and residuals."""
+def segment(I0, seeds, params: OracleParams | None = None, nsteps: int = 10,
+            omp: bool = False):
+    """The whole pipeline; returns (u, info) with per-step sweeps and residuals.
+    omp: run it on the OpenMP build (timing only)."""
     params = params or OracleParams()
     I0 = _f64(I0)
     xyz, fr, n = _seeds(seeds)
@@ -258,7 +273,7 @@ def segment(I0, seeds, params: OracleParams | None = None, nsteps: int = 10):
     iters = np.zeros(max(nsteps, 1), dtype=np.int32)
     res = np.zeros(max(nsteps, 1))
     P = params.c_struct()
-    st = lib().or_segment(_dims(I0.shape), _d(I0), _d(xyz), _i(fr), n, C.byref(P), int(nsteps),
+    st = lib(omp).or_segment(_dims(I0.shape), _d(I0), _d(xyz), _i(fr), n, C.byref(P), int(nsteps),
                           _d(u), _i(iters), _d(res))
     return u, {"status": st, "iters": iters[:nsteps].tolist(), "res_rel": res[:nsteps].tolist()}
 

@@ -10,7 +10,10 @@
  *
  * Style: slow, single-threaded and direct.  Every function follows the
  * formula it cites, in the paper's order and notation, so that it can be
- * checked against the paper by eye.  All arithmetic is double precision; the
+ * checked against the paper by eye.  (A second library built from this file
+ * with SEG4D_ORACLE_OMP splits the SOR sweeps' frame loop among OpenMP
+ * threads, as the paper's OpenMP program does; it serves only as a timed CPU
+ * baseline, and a test checks that it reaches the same solutions.)  All arithmetic is double precision; the
  * file is compiled with -ffp-contract=off so that x86 and Arm hosts give the
  * same bits.
  *
@@ -265,8 +268,12 @@ static double residual_norm_padded(const pgrid *g, const double *diag, const dou
                                    const double *b, const double *up)
 {
     double s = 0.0;
-    long v = 0;
-    for (int l = 0; l < g->n[3]; ++l)
+    const long frame = (long)g->n[0] * g->n[1] * g->n[2];
+#ifdef SEG4D_ORACLE_OMP
+#pragma omp parallel for schedule(static) reduction(+ : s)
+#endif
+    for (int l = 0; l < g->n[3]; ++l) {
+        long v = (long)l * frame;
         for (int k = 0; k < g->n[2]; ++k)
             for (int j = 0; j < g->n[1]; ++j)
                 for (int i = 0; i < g->n[0]; ++i, ++v) {
@@ -278,13 +285,35 @@ static double residual_norm_padded(const pgrid *g, const double *diag, const dou
                     }
                     s += acc * acc;
                 }
+    }
     return sqrt(s);
+}
+
+/* One relaxation (Eq. 5.33 with the Gauss-Seidel value of Eq. gsee) of the
+ * interior voxel v at padded index p. */
+static void relax_padded(const pgrid *g, const double *diag, const double *off, const double *b,
+                         double *up, double omega, long v, long p)
+{
+    double acc = b[v];
+    for (int f = 0; f < 8; ++f) {
+        long sd = (f & 1) ? g->st[f >> 1] : -g->st[f >> 1];
+        acc += off[v * 8 + f] * up[p + sd];
+    }
+    double ubar = acc / diag[v];
+    up[p] = omega * ubar + (1.0 - omega) * up[p];
 }
 
 /* SOR in lexicographic order (Eq. 5.33 with the Gauss-Seidel value of
  * Eq. gsee): neighbours already visited in this sweep carry their new value.
  * Stops when ||b - A u||_2 <= tol * ||b||_2, tested before the first sweep and
- * then every check_every sweeps. */
+ * then every check_every sweeps.
+ *
+ * Built with SEG4D_ORACLE_OMP (a separate library, used only as a timed CPU
+ * baseline, never by the tests' pins), the sweep follows the paper's OpenMP
+ * scheme instead: the frame loop is split among threads, and the RED-BLACK
+ * ordering of Section 3.7 (red: even index sum) makes that split exact.  The
+ * iterates differ from the lexicographic ones; the solution of the system is
+ * the same. */
 static int sor_padded(const pgrid *g, const double *diag, const double *off, const double *b,
                       double *up, double omega, double tol, int max_iters, int check_every,
                       int *iters, double *res_rel)
@@ -299,20 +328,28 @@ static int sor_padded(const pgrid *g, const double *diag, const double *off, con
     if (!(rn <= tol * bn)) {
         status = OR_NOT_CONVERGED;
         for (it = 1; it <= max_iters; ++it) {
+#ifdef SEG4D_ORACLE_OMP
+            const long frame = (long)g->n[0] * g->n[1] * g->n[2];
+            for (int colour = 0; colour < 2; ++colour) {
+#pragma omp parallel for schedule(static)
+                for (int l = 0; l < g->n[3]; ++l) {
+                    long v = (long)l * frame;
+                    for (int k = 0; k < g->n[2]; ++k)
+                        for (int j = 0; j < g->n[1]; ++j)
+                            for (int i = 0; i < g->n[0]; ++i, ++v)
+                                if (((i + j + k + l) & 1) == colour)
+                                    relax_padded(g, diag, off, b, up, omega, v,
+                                                 pg_at(g, i, j, k, l));
+                }
+            }
+#else
             long v = 0;
             for (int l = 0; l < g->n[3]; ++l)
                 for (int k = 0; k < g->n[2]; ++k)
                     for (int j = 0; j < g->n[1]; ++j)
-                        for (int i = 0; i < g->n[0]; ++i, ++v) {
-                            long p = pg_at(g, i, j, k, l);
-                            double acc = b[v];
-                            for (int f = 0; f < 8; ++f) {
-                                long sd = (f & 1) ? g->st[f >> 1] : -g->st[f >> 1];
-                                acc += off[v * 8 + f] * up[p + sd];
-                            }
-                            double ubar = acc / diag[v];
-                            up[p] = omega * ubar + (1.0 - omega) * up[p];
-                        }
+                        for (int i = 0; i < g->n[0]; ++i, ++v)
+                            relax_padded(g, diag, off, b, up, omega, v, pg_at(g, i, j, k, l));
+#endif
             if (it % check_every == 0 || it == max_iters) {
                 rn = residual_norm_padded(g, diag, off, b, up);
                 if (rn <= tol * bn) { status = OR_OK; break; }
@@ -324,6 +361,15 @@ static int sor_padded(const pgrid *g, const double *diag, const double *off, con
     if (res_rel) *res_rel = bn > 0.0 ? rn / bn : rn;
     return status;
 }
+
+/* Threads the sweeps use: 1, or OpenMP's maximum in the SEG4D_ORACLE_OMP
+ * build. */
+#ifdef SEG4D_ORACLE_OMP
+#include <omp.h>
+int or_threads(void) { return omp_get_max_threads(); }
+#else
+int or_threads(void) { return 1; }
+#endif
 
 /* Solve diag/off system with zero Dirichlet ghosts; u holds the initial
  * guess on entry and the iterate on exit. */
@@ -555,7 +601,7 @@ int or_assemble(const int *dims, const double *u, const double *G, const double 
 }
 
 /* ------------------------------------------------------------------------ */
-/* the whole segmentation (Section 3.6, "Brief overview")                    */
+/* the whole segmentation (Section 3.5, "Brief overview")                    */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {

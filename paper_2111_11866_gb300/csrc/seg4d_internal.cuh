@@ -1,6 +1,6 @@
 // seg4d_internal.cuh -- device data layout and kernel launchers of libseg4d.
 //
-// Layout ("colour-split rows").  The red-black ordering of Section 3.2 colours
+// Layout ("colour-split rows").  The red-black ordering of Section 3.7 colours
 // voxel (i,j,k,l) red when i+j+k+l is even.  Every array that a sweep touches
 // is stored as two half arrays, red then black.  Row r = j + n2*(k + n3*l)
 // holds the voxels of one x-line; inside a row the voxels of one colour are

@@ -1,5 +1,5 @@
 // solve_kernels.cu -- per-step coefficients (Eqs. 111th, new1), the red-black
-// SOR half sweep (Eqs. 5.33, gsee with the red-black ordering of Section 3.2),
+// SOR half sweep (Eqs. 5.33, gsee with the red-black ordering of Section 3.7),
 // the residual of the step system and the FP64 reductions of the stopping
 // test.  Layout: seg4d_internal.cuh.
 #include <algorithm>

@@ -143,3 +143,20 @@ def test_assembly_closed_form_for_constant_u(h):
     hd2 = np.array([h[f // 2] ** 2 for f in range(8)])
     np.testing.assert_allclose(off[inner], TAU / hd2 * G[inner], rtol=1e-14)
     np.testing.assert_allclose(diag[inner], 1.0 + (TAU / hd2 * G[inner]).sum(-1), rtol=1e-14)
+
+
+def test_openmp_build_reaches_the_same_solution():
+    """The OpenMP build (a timed CPU baseline: the paper's frame-split
+    red-black sweeps) solves the same systems: the whole pipeline agrees with
+    the plain build's to the 1e-12 solve, with similar sweep counts."""
+    from paper_2111_11866_gb300 import synth
+    O.build(omp=True)
+    c = synth.small_nuclei(3, n=(24, 20, 10, 5), count=3, nsteps=2)
+    P = O.OracleParams()
+    img = c.image.astype(np.float64)
+    u0, i0 = O.segment(img, c.seeds, P, nsteps=2)
+    u1, i1 = O.segment(img, c.seeds, P, nsteps=2, omp=True)
+    assert i0["status"] == i1["status"] == O.OR_OK
+    assert np.abs(u1 - u0).max() <= 1e-9 * max(1.0, np.abs(u0).max())
+    assert all(0.5 * a <= b <= 2 * a for a, b in zip(i0["iters"], i1["iters"]))
+    assert O.threads(False) == 1 and O.threads(True) >= 1
