@@ -141,6 +141,23 @@ def _crop_case(case, n=(64, 64, 32, 8)):
     return img, s[keep]
 
 
+def _host_cpu():
+    """nproc, architecture and CPU model of the host the CPU baselines ran on."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "processor name") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "model": model}
+
+
 def oracle_sample(case, params, nsteps=1, omp=False):
     """The FP64 oracle, as it stands, on a crop of the workload: returns
     (voxel-sweeps per second, description, seconds).  omp: its OpenMP build
@@ -189,7 +206,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(case),
             "cpu_baseline": {"value": value, "unit": "voxel-sweeps/s", "cores": 1,
-                             "kind": "oracle", "sample": desc},
+                             "kind": "oracle", "sample": desc, "host": _host_cpu()},
             "e2e": {"value": value, "unit": "voxel-sweeps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -587,7 +604,8 @@ def main():
     cpu = cpu_omp = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, _, _ = oracle_sample(case, params)
-        cpu = {"value": v, "unit": "voxel-sweeps/s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": "voxel-sweeps/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "host": _host_cpu()}
         try:
             v, desc, _, cores = oracle_sample(case, params, omp=True)
             cpu_omp = {"value": v, "unit": "voxel-sweeps/s", "cores": cores,

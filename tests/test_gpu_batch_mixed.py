@@ -67,3 +67,33 @@ def test_precision_fixed_while_windows_resident():
         with pytest.raises(_lib.Seg4DError):
             b.set_params(precision=1)
     assert _lib.Batch.window_bytes((24, 24, 24, 4), 1, 1) > _lib.Batch.window_bytes((24, 24, 24, 4))
+
+
+def test_sampled_config4_windows_match_oracle():
+    """Windows of the batched workload itself (per-nucleus windows of the
+    medium generator, cubic edge 24-64, 8-16 frames, 30 steps), in the mode
+    the bench runs them (mixed precision, all in one batch): the four smallest
+    of the first 64 windows against the FP64 oracle, per-voxel bound and
+    labels outside a one-voxel band."""
+    from gpu_common import label_mismatch_outside_band
+    wins = synth.windows(64)
+    pick = sorted(range(len(wins)), key=lambda k: wins[k][0].size)[:4]
+    specs = {k: wins[k] for k in pick}
+    p = _lib.Params.defaults()
+    p.precision = 1
+    with _lib.Batch(4 << 30, 16, params=p) as b:
+        ids = {k: b.add(*v) for k, v in specs.items()}
+        for _ in range(max(v[2] for v in specs.values())):
+            b.advance()
+        res = {}
+        for k, wid in ids.items():
+            info = b.poll(wid)
+            assert info["state"] == "done" and info["steps_done"] == specs[k][2], info
+            res[k] = b.read_u(wid)
+    P = oracle_params(p)
+    for k, (img, seeds, nsteps) in specs.items():
+        ref, info = O.segment(img.astype(np.float64), seeds, P, nsteps=nsteps)
+        assert info["status"] == O.OR_OK
+        err = np.abs(res[k] - ref).max()
+        assert err <= REL_TOL * np.abs(ref).max(), (k, img.shape, err)
+        assert label_mismatch_outside_band(res[k], ref) == 0, k
