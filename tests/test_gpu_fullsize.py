@@ -129,3 +129,43 @@ def test_large_workload_rows_and_min_max():
         seg.set_seeds(seeds)
         seg.setup()
         _check_solve(seg, p, seeds, 300, np.random.default_rng(22))
+
+
+def test_tiled_plane_order_reaches_every_plane():
+    """A grid whose planes are large enough for the tiled plane order to
+    group the 9 z-planes in tiles of 2 (a ragged last tile with a hole), with
+    rows of 552 slots per colour (nine 64-slot chunks, the last one ragged):
+    after the first step solve, oracle rows at sampled voxels of every (k, l)
+    plane and at the grid faces, and the min-max bound over the whole grid.
+    A plane that the sweeps, the coefficient pass or the defect pass skipped
+    or visited twice fails the row check there."""
+    dims = (1100, 600, 9, 2)
+    n1, n2, n3, n4 = dims
+    img = synth.random_field(31, dims, 0.0, 0.3)
+    seeds = [(550, 300, 4, 0), (200, 100, 2, 1), (900, 500, 7, 1)]
+    p = _lib.Params.defaults()
+    p.r_ball = p.R_init = 6.0
+    rng = np.random.default_rng(23)
+    with _lib.Seg4D(dims, params=p) as seg:
+        seg.set_image(img)
+        seg.set_seeds(seeds)
+        seg.setup()
+        b = seg.read_u()
+        info = seg.solve()
+        assert info["status"] == _lib.OK and info["res_rel"] <= p.tol, info
+        u = seg.read_u()
+        res = info["res_l2"]
+        lo = min(0.0, float(b.min())) - res
+        hi = max(0.0, float(b.max())) + res
+        assert float(u.min()) >= lo - 1e-6 and float(u.max()) <= hi + 1e-6
+        Is0 = seg.read_field("Isig0")
+        IsTH = seg.read_field("IsigTH")
+    pts = _samples(b.shape, [], 40, rng)
+    for l in range(n4):
+        for k in range(n3):
+            for _ in range(3):
+                pts.append((l, k, int(rng.integers(0, n2)), int(rng.integers(0, n1))))
+    worst = 0.0
+    for r, mag in _row_residuals(pts, b, u, Is0, IsTH, p):
+        worst = max(worst, abs(r) - (res + ROW_REL * mag))
+    assert worst <= 0.0, worst
