@@ -69,18 +69,6 @@ __host__ __device__ inline long long slot_of(const Layout &L, int i, int j, int 
     return (long long)row * L.P + (i >> 1);
 }
 
-// u-like field read with zero Dirichlet ghosts (Eq. first11 with u^D = 0).
-__device__ inline float ld_dirichlet(const Layout &L, const float *__restrict__ a, int i, int j,
-                                     int k, int l)
-{
-    if ((unsigned)i >= (unsigned)L.n1 || (unsigned)j >= (unsigned)L.n2 ||
-        (unsigned)k >= (unsigned)L.n3 || (unsigned)l >= (unsigned)L.n4)
-        return 0.0f;
-    int c;
-    long long s = slot_of(L, i, j, k, l, c);
-    return a[c * L.S + s];
-}
-
 __device__ inline int clampi(int a, int n) { return a < 0 ? 0 : (a >= n ? n - 1 : a); }
 
 // image read with replicated ghosts (zero Neumann data for images).

@@ -106,6 +106,12 @@ void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *
 // (error) and ctrl[1] (abort) and all CTAs leave; the host reports
 // SEG4D_ERR_TIMEOUT.
 //
+// Visibility: an item's stores are published by one thread after the CTA
+// barrier, with a gpu-scope fence and a release store of done[T].  The next
+// CTA acquires each counter it depends on (ld.acquire.gpu) before its own
+// barrier, so every thread's later plain loads, L1 included, see the stores
+// (release -> acquire -> barrier orders them in the PTX memory model).
+//
 // ctrl layout (u32, zeroed before every launch): [0] ticket, [1] abort,
 // [2] error, [3] flag of the timeout test hook (never set), [4 ..] done[Tf].
 #ifndef SEG4D_WAVE_PASS

@@ -121,25 +121,13 @@ __device__ __forceinline__ void decode_item(const ItemDecode &D, const Layout &L
     rp.p = (rp.j + rp.k + rp.l) & 1;
 }
 
-// Sum over the 8 faces of  w_f * x_nb(f)  for the voxel in slot s of row `row`
-// (colour C, row parity p); neighbours outside the grid are Dirichlet zeros.
-// Red voxels own their 8 face weights; a black voxel reads each weight from
-// the red voxel across the face (opposite face index).
-// u loads: plain, or at L2 only (ld.global.cg) where other CTAs of the same
-// launch write u, so that no stale L1 line can be read.
-template <bool kCG>
-__device__ __forceinline__ float ldu(const float *p)
-{
-    return kCG ? __ldcg(p) : *p;
-}
-
 // face weight load: FP32, or BF16 widened to FP32
 __device__ __forceinline__ float ldw(const float *p) { return *p; }
 __device__ __forceinline__ float ldw(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 
 // Relaxation arithmetic with every rounding explicit (no contraction left to
-// the compiler), so that all sweep kernels -- one voxel or two per thread,
-// fused or not -- produce the same bits:
+// the compiler), so that all sweep kernels -- per colour or fused, single
+// grid or batched -- produce the same bits:
 //   acc = sum over faces of w_f x_f (products rounded, fixed addition tree),
 //   x  <- x + omega (B + G acc - x).
 __device__ __forceinline__ float sum8(float t0, float t1, float t2, float t3, float t4, float t5,
@@ -152,42 +140,6 @@ __device__ __forceinline__ float sum8(float t0, float t1, float t2, float t3, fl
 __device__ __forceinline__ float relax(float x, float B, float G, float acc, float omega)
 {
     return __fmaf_rn(omega, __fsub_rn(__fmaf_rn(G, acc, B), x), x);
-}
-
-template <int C, bool kCG = false, typename WT = float>
-__device__ __forceinline__ float neighbour_sum(const Layout &L, const float *__restrict__ xo,
-                                               const WT *__restrict__ W, int row, int s,
-                                               const RowPos &rp)
-{
-    const long long S = L.S;
-    const long long rb = (long long)row * L.P;
-    const long long q = rb + s;
-    const long long dy = L.P;
-    const long long dz = (long long)L.n2 * L.P;
-    const long long dt = (long long)L.n2 * L.n3 * L.P;
-    float t0, t1, t2, t3, t4, t5, t6, t7;
-    if (C == 0) {
-        const int sxm = s - 1 + rp.p, sxp = s + rp.p;
-        t0 = sxm >= 0 ? __fmul_rn(ldw(W + 0 * S + q), ldu<kCG>(xo + rb + sxm)) : 0.0f;
-        t1 = sxp < L.P ? __fmul_rn(ldw(W + 1 * S + q), ldu<kCG>(xo + rb + sxp)) : 0.0f;
-        t2 = rp.j > 0 ? __fmul_rn(ldw(W + 2 * S + q), ldu<kCG>(xo + q - dy)) : 0.0f;
-        t3 = rp.j + 1 < L.n2 ? __fmul_rn(ldw(W + 3 * S + q), ldu<kCG>(xo + q + dy)) : 0.0f;
-        t4 = rp.k > 0 ? __fmul_rn(ldw(W + 4 * S + q), ldu<kCG>(xo + q - dz)) : 0.0f;
-        t5 = rp.k + 1 < L.n3 ? __fmul_rn(ldw(W + 5 * S + q), ldu<kCG>(xo + q + dz)) : 0.0f;
-        t6 = rp.l > 0 ? __fmul_rn(ldw(W + 6 * S + q), ldu<kCG>(xo + q - dt)) : 0.0f;
-        t7 = rp.l + 1 < L.n4 ? __fmul_rn(ldw(W + 7 * S + q), ldu<kCG>(xo + q + dt)) : 0.0f;
-    } else {
-        const int sxm = s - rp.p, sxp = s + 1 - rp.p;
-        t0 = sxm >= 0 ? __fmul_rn(ldw(W + 1 * S + rb + sxm), ldu<kCG>(xo + rb + sxm)) : 0.0f;
-        t1 = sxp < L.P ? __fmul_rn(ldw(W + 0 * S + rb + sxp), ldu<kCG>(xo + rb + sxp)) : 0.0f;
-        t2 = rp.j > 0 ? __fmul_rn(ldw(W + 3 * S + q - dy), ldu<kCG>(xo + q - dy)) : 0.0f;
-        t3 = rp.j + 1 < L.n2 ? __fmul_rn(ldw(W + 2 * S + q + dy), ldu<kCG>(xo + q + dy)) : 0.0f;
-        t4 = rp.k > 0 ? __fmul_rn(ldw(W + 5 * S + q - dz), ldu<kCG>(xo + q - dz)) : 0.0f;
-        t5 = rp.k + 1 < L.n3 ? __fmul_rn(ldw(W + 4 * S + q + dz), ldu<kCG>(xo + q + dz)) : 0.0f;
-        t6 = rp.l > 0 ? __fmul_rn(ldw(W + 7 * S + q - dt), ldu<kCG>(xo + q - dt)) : 0.0f;
-        t7 = rp.l + 1 < L.n4 ? __fmul_rn(ldw(W + 6 * S + q + dt), ldu<kCG>(xo + q + dt)) : 0.0f;
-    }
-    return sum8(t0, t1, t2, t3, t4, t5, t6, t7);
 }
 
 // ------------------------------------------------ N voxels per thread
@@ -354,9 +306,9 @@ __device__ __forceinline__ void gather_core(const Layout &L, const float *__rest
     }
 }
 
-// Neighbour sums acc[m] = sum_f w_f x_nb(f) of a group (see gather_core),
-// with the arithmetic of neighbour_sum (products rounded, fixed addition
-// tree, a face outside the grid contributes exactly 0).
+// Neighbour sums acc[m] = sum_f w_f x_nb(f) of a group (see gather_core):
+// products rounded, the fixed addition tree of sum8, a face outside the grid
+// contributes exactly 0.
 template <int C, typename WT, int N>
 __device__ __forceinline__ void gather_vec(const Layout &L, const float *__restrict__ x,
                                            const WT *__restrict__ W, bool act, int row, int s0,
@@ -431,7 +383,7 @@ __device__ __forceinline__ void flux_residual_vec(const Layout &L, const float *
 
 // One colour-C relaxation of the N voxels of a group (see gather_vec):
 // x <- x + omega (B + G acc - x) with B and G the [2][S] per-voxel
-// coefficients, the arithmetic of neighbour_sum + relax.  kUnit: G = 1 (the
+// coefficients, the arithmetic of gather_vec + relax.  kUnit: G = 1 (the
 // symmetrically scaled system, where no G is stored or read).  Slots past the
 // row end (i >= n1) are padding and keep their value (zero).
 template <int C, typename WT, int N, bool kUnit = false>
