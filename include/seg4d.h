@@ -11,7 +11,7 @@
  * solves the linear system of Eq. new1 (Eq. new for equal h) built with the
  * reduced diamond-cell gradients of Section 3.2 and the coefficients of
  * Eq. 111th, by red-black SOR (Eqs. 5.33, gsee and the red-black ordering of
- * Section 3.2), and then rescales u locally (Remark, Eq. 841).
+ * Section 3.7), and then rescales u locally (Remark, Eq. 841).
  *
  * Conventions shared by every entry point:
  *  - Arrays are 4D, x fastest: index ((l*n3 + k)*n2 + j)*n1 + i for 0-based
