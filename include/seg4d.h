@@ -172,7 +172,9 @@ seg4d_status seg4d_set_params(seg4d *h, const seg4d_params *p);
 
 /* Copy the 4D image I0 (n = n1*n2*n3*n4 floats).  Marks the image-derived
  * set-up (thresholding, presmoothing, G) for recomputation.
- * Errors: INVALID (n mismatch, NULL, non-finite values), CUDA. */
+ * Errors: INVALID (n mismatch, NULL, non-finite values -- checked on the
+ * device after the copy, so the handle then has no image until the next
+ * successful call), CUDA. */
 seg4d_status seg4d_set_image(seg4d *h, const float *I0, size_t n, int on_device);
 
 /* Copy the seeds (Section 3.1, the centres C_theta).  Marks the set-up for

@@ -59,7 +59,9 @@ struct seg4d {
     double *scal = nullptr;        // 8 doubles: reduced records
     double *host_scal = nullptr;   // pinned mirror of scal
     unsigned *wave_ctrl = nullptr; // fused-sweep control block: 4 + tiles u32
-    unsigned *host_wave = nullptr; // pinned: error flag of the last fused sweep
+    unsigned *host_wave = nullptr; // pinned: [0] error flag of the last fused sweep,
+                                   // [1] non-finite flag of the last checked input
+    unsigned *d_check = nullptr;   // device flag: a checked input held a non-finite value
     // defect-correction solve (allocated at the first solve that needs them)
     void *Wb = nullptr;            // mixed: bf16 [8][S] face weights by red end
     float *gb = nullptr;           // mixed: c / D_b, [2][S]
@@ -203,6 +205,7 @@ void free_all(seg4d *h)
     cudaFree(h->partials);
     cudaFree(h->scal);
     cudaFree(h->wave_ctrl);
+    cudaFree(h->d_check);
     if (h->host_wave) cudaFreeHost(h->host_wave);
     cudaFree(h->Wb);
     cudaFree(h->gb);
@@ -586,7 +589,10 @@ seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
     return SEG4D_OK;
 }
 
-seg4d_status copy_in(seg4d *h, const float *src, size_t n, int on_device, float *dst_split)
+// check_finite: the split kernel flags non-finite values; the flag lands in
+// host_wave[1] once the stream has reached this point
+seg4d_status copy_in(seg4d *h, const float *src, size_t n, int on_device, float *dst_split,
+                     bool check_finite = false)
 {
     if (!src) return fail(h, SEG4D_ERR_INVALID, "NULL input pointer");
     if ((long long)n != nvox(h)) return fail(h, SEG4D_ERR_INVALID, "array size does not match dims");
@@ -595,9 +601,14 @@ seg4d_status copy_in(seg4d *h, const float *src, size_t n, int on_device, float 
         CK(cudaMemcpyAsync(h->stage, src, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
         nat = h->stage;
     }
-    launch_split_from_natural(h->L, nat, dst_split, h->stream);
+    if (check_finite) CK(cudaMemsetAsync(h->d_check, 0, sizeof(unsigned), h->stream));
+    launch_split_from_natural(h->L, nat, dst_split, check_finite ? h->d_check : nullptr,
+                              h->stream);
     h->launches += 1;
     CK_LAUNCH("split");
+    if (check_finite)
+        CK(cudaMemcpyAsync(h->host_wave + 1, h->d_check, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                           h->stream));
     return SEG4D_OK;
 }
 
@@ -721,6 +732,7 @@ seg4d_status seg4d_create_ex(const seg4d_dims *dims, void *cuda_stream, int flag
         {(void **)&h->partials, 3 * kPartCap * sizeof(double)},
         {(void **)&h->scal, 8 * sizeof(double)},
         {(void **)&h->wave_ctrl, (4 + (size_t)wave_tiles(L)) * sizeof(unsigned)},
+        {(void **)&h->d_check, 4 * sizeof(unsigned)},
     };
     if (h->lean) {
         // the solve's scratch exists from the start; staging and the image
@@ -825,13 +837,14 @@ seg4d_status seg4d_set_image(seg4d *h, const float *I0, size_t n, int on_device)
     if (!h) return SEG4D_ERR_INVALID;
     seg4d_status st = use_device(h);
     if (st) return st;
-    if (!on_device && I0 && (long long)n == nvox(h)) {
-        for (size_t v = 0; v < n; ++v)
-            if (!std::isfinite(I0[v])) return fail(h, SEG4D_ERR_INVALID, "image has NaN/Inf");
-    }
     if (h->lean) h->I0 = h->G;
-    if ((st = copy_in(h, I0, n, on_device, h->I0))) return st;
+    if ((st = copy_in(h, I0, n, on_device, h->I0, true))) return st;
     CK(cudaStreamSynchronize(h->stream));
+    if (h->host_wave[1] != 0u) {   // the copy overwrote the old image
+        h->has_image = false;
+        h->setup_dirty = true;
+        return fail(h, SEG4D_ERR_INVALID, "image has NaN/Inf; the handle has no image now");
+    }
     h->has_image = true;
     h->img_live = true;
     h->setup_dirty = true;

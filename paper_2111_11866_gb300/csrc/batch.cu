@@ -1173,7 +1173,7 @@ seg4d_status seg4d_batch_add(seg4d_batch *b, const seg4d_dims *dims, const float
         BCK(cudaMemcpyAsync(w.Is0, image, n * sizeof(float), cudaMemcpyHostToDevice, b->stream));
         nat = w.Is0;
     }
-    launch_split_from_natural(w.L, nat, w.I0, b->stream);
+    launch_split_from_natural(w.L, nat, w.I0, nullptr, b->stream);
     b->launches += 1;
     BCK(cudaGetLastError());
     BCK(cudaStreamSynchronize(b->stream));

@@ -117,7 +117,9 @@ struct Ghost {
 
 // ---------------------------------------------------------------- launchers
 // set-up (setup_kernels.cu)
-void launch_split_from_natural(const Layout &L, const float *nat, float *split, cudaStream_t st);
+// bad (nullable): a device flag set to 1 when an input value is not finite
+void launch_split_from_natural(const Layout &L, const float *nat, float *split, unsigned *bad,
+                               cudaStream_t st);
 void launch_natural_from_split(const Layout &L, const float *split, float *nat, cudaStream_t st);
 void launch_faces_natural_from_split(const Layout &L, const float *split8, float *nat8,
                                      cudaStream_t st);

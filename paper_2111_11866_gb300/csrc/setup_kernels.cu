@@ -19,9 +19,10 @@ namespace seg4d_impl {
 
 // ------------------------------------------------------------ conversions
 
-// natural (x fastest) -> colour-split; one thread per natural voxel
+// natural (x fastest) -> colour-split; one thread per natural voxel.  bad
+// (nullable): set to 1 when a value is not finite.
 __global__ void k_split_from_natural(Layout L, const float *__restrict__ nat,
-                                     float *__restrict__ split)
+                                     float *__restrict__ split, unsigned *__restrict__ bad)
 {
     const long long n = (long long)L.n1 * L.R;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -34,7 +35,9 @@ __global__ void k_split_from_natural(Layout L, const float *__restrict__ nat,
         const int l = (int)(t / L.n3);
         int c;
         const long long s = slot_of(L, i, j, k, l, c);
-        split[c * L.S + s] = nat[v];
+        const float x = nat[v];
+        split[c * L.S + s] = x;
+        if (bad && !isfinite(x)) atomicOr(bad, 1u);
     }
 }
 
@@ -117,9 +120,10 @@ static int conv_blocks(const Layout &L)
     return (int)(b < 1 ? 1 : b);
 }
 
-void launch_split_from_natural(const Layout &L, const float *nat, float *split, cudaStream_t st)
+void launch_split_from_natural(const Layout &L, const float *nat, float *split, unsigned *bad,
+                               cudaStream_t st)
 {
-    k_split_from_natural<<<conv_blocks(L), 256, 0, st>>>(L, nat, split);
+    k_split_from_natural<<<conv_blocks(L), 256, 0, st>>>(L, nat, split, bad);
 }
 
 void launch_natural_from_split(const Layout &L, const float *split, float *nat, cudaStream_t st)

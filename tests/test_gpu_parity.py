@@ -192,6 +192,31 @@ def test_errors_are_reported():
             s.set_image(np.zeros(10, np.float32))
 
 
+def test_non_finite_image_is_refused_on_the_device():
+    """The image is checked for NaN/Inf after the copy, for host and device
+    input alike; a refused image leaves the handle without an image."""
+    import torch
+    c = synth.small_nuclei(seed=5, n=(24, 20, 12, 4), count=2, nsteps=1)
+    with _lib.Seg4D(c.dims) as s:
+        s.set_image(c.image)
+        s.set_seeds(c.seeds)
+        bad = c.image.copy()
+        bad[1, 2, 3, 4] = np.inf
+        with pytest.raises(_lib.Seg4DError) as e:
+            s.set_image(bad)
+        assert e.value.status == _lib.ERR_INVALID
+        with pytest.raises(_lib.Seg4DError) as e:
+            s.step(1)
+        assert e.value.status == _lib.ERR_STATE
+        bad_d = torch.from_numpy(c.image).cuda()
+        bad_d[0, 0, 0, 0] = float("nan")
+        with pytest.raises(_lib.Seg4DError) as e:
+            s.set_image(bad_d)
+        assert e.value.status == _lib.ERR_INVALID
+        s.set_image(torch.from_numpy(c.image).cuda())
+        assert s.step(1)["status"] == _lib.OK
+
+
 def test_not_converged_is_reported_and_u_kept():
     c = synth.small_nuclei(seed=5, n=(24, 20, 12, 4), count=2, nsteps=1)
     p = _lib.Params.defaults()
