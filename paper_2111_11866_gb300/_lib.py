@@ -178,9 +178,9 @@ def _ptr(a, n_expected):
             raise ValueError("expected a contiguous tensor")
         if a.numel() != n_expected:
             raise ValueError(f"expected {n_expected} elements, got {a.numel()}")
-        if a.is_cuda:
-            return C.c_void_p(a.data_ptr()), 1, a
-        a = a.numpy()
+        # device tensors stay on the device; CPU tensors (pinned or not) are
+        # host memory, read or written in place
+        return C.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0), a
     arr = np.ascontiguousarray(a, dtype=np.float32)
     if arr.size != n_expected:
         raise ValueError(f"expected {n_expected} elements, got {arr.size}")

@@ -59,3 +59,18 @@ def test_default_params_and_device_bytes(lib):
     # 88 bytes per voxel of grid state plus 32 of the FP32 solve's arrays
     assert 110 * 33554432 < nb < 130 * 33554432
     assert _lib.Seg4D.device_bytes((0, 1, 1, 1)) == 0
+
+
+def test_host_tensors_are_used_in_place():
+    """CPU tensors (pinned ones included) are passed by pointer as host memory,
+    so reads land in the caller's tensor; numpy arrays likewise."""
+    import numpy as np
+    import torch
+    t = torch.zeros(2, 3, 4, 5)
+    p, dev, keep = _lib._ptr(t, 120)
+    assert dev == 0 and keep is t and p.value == t.data_ptr()
+    a = np.zeros((2, 3, 4, 5), np.float32)
+    p, dev, keep = _lib._ptr(a, 120)
+    assert dev == 0 and keep is a
+    with pytest.raises(TypeError):
+        _lib._ptr(torch.zeros(120, dtype=torch.float64), 120)
