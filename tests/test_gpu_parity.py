@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
 same seeded inputs.
 
-Bars (derived in the design doc):
+Bars (from the arithmetic of each stage):
 - integer and copy work is bit-exact: ball owners, the thresholded image;
 - the FP32 presmoothing solves stop at ||r|| <= 1e-6 ||b|| (the oracle at
   1e-12): |diff| <= 2e-5 max|I|;

@@ -7,12 +7,16 @@ semi-implicit system (Eq. new), the SOR solve and the ghost-cell boundary
 handling at once: a dropped tangential term, a wrong Abar average or a wrong
 power of h changes the order of convergence.
 
-Reading (recorded in DESIGN.md): the table labels its runs "eps = h^2"; its
-orders are reproduced when h^2 is the quantity added under the square root,
-i.e. eps = h in the notation of Eq. 3rd.  With that reading the EOC column is
-matched to within 0.05.  The absolute errors come out a near-constant factor
-of about 2.45 below the printed ones (same shape, unexplained normalisation),
-so absolute values are pinned only up to that constant.
+Reading: the table labels its runs "eps = h^2"; its orders are reproduced
+when h^2 is the quantity added under the square root, i.e. eps = h in the
+notation of Eq. 3rd.  With that reading the EOC column is matched to within
+0.05, and no other multiple of h does that (0.5 h, 2 h, 3 h and 6 h give
+orders 2.26/2.13, 1.39/1.61, 1.09/1.34, 0.70/0.80).  The absolute errors
+come out a near-constant factor of 2.41-2.48 below the printed ones (same
+shape).  Neither the final-time L2 norm nor the root of the summed per-step
+norms reproduces the printed values, and rescaling u by the 1/6 of the exact
+solution is equivalent to eps/6, which breaks the orders; so absolute values
+are pinned only up to that constant.
 """
 import math
 import os

@@ -177,3 +177,48 @@ def test_threshold_tie_goes_to_beta():
     I0 = np.array([0.0, 0.5, 1.0, 0.25])[None, None, None]
     ITH = O.threshold(I0, [(1, 0, 0, 0)], r=2.0, lam=0.5).reshape(-1)
     np.testing.assert_array_equal(ITH, [0.0, 1.0, 1.0, 0.0])
+
+
+# --------------------------------------------------------------------------
+# overlapping balls: statistics over the whole ball, applied to owned voxels
+# --------------------------------------------------------------------------
+#
+# Section 3.1 defines alpha_m, beta_m as the min and max of I0 over the whole
+# ball B(c_m, r), and the Remark on local rescaling (Section 3.2) defines
+# mu_m, xi_m over the whole ball too.  Where balls overlap, a voxel follows
+# its nearest seed, but the statistics of a ball still include the voxels of
+# the ball that another seed owns.  In the two cases below the extremes of
+# each ball sit on voxels owned by the other seed, so statistics taken over
+# the owned voxels only give different values.  Geometry: seeds at x = 2 and
+# x = 7 on a line of 10 voxels, r = 3; ball 0 = voxels 0..5, ball 1 = voxels
+# 4..9; voxel 4 is nearer seed 0, voxel 5 nearer seed 1.
+
+
+def test_threshold_overlap_uses_whole_ball_statistics():
+    I0 = np.array([0.02, 0.4, 0.5, 0.35, 0.05, 0.95, 0.6, 0.7, 0.5, 1.0])[None, None, None]
+    seeds = [(2, 0, 0, 0), (7, 0, 0, 0)]
+    own = O.owner(I0.shape, seeds, r=3.0).reshape(-1)
+    assert own.tolist() == [0, 0, 0, 0, 0, 1, 1, 1, 1, 1]
+    ITH = O.threshold(I0, seeds, r=3.0, lam=0.5).reshape(-1)
+    # ball 0: alpha 0.02 (voxel 0), beta 0.95 (voxel 5, owned by seed 1):
+    #   TH = 0.485, so 0.5 -> 0.95 and 0.4, 0.35, 0.05 -> 0.02
+    # ball 1: alpha 0.05 (voxel 4, owned by seed 0), beta 1.0 (voxel 9):
+    #   TH = 0.525, so 0.5 -> 0.05 and 0.95, 0.6, 0.7, 1.0 -> 1.0
+    expect = [0.02, 0.02, 0.95, 0.02, 0.02, 1.0, 1.0, 1.0, 0.05, 1.0]
+    np.testing.assert_array_equal(ITH, expect)
+    # statistics over the owned voxels would give ball 0 beta = 0.5 (TH 0.26)
+    # and ball 1 alpha = 0.5: voxel 1 would map to 0.5 and voxel 8 to 0.5
+    assert ITH[1] != 0.5 and ITH[8] != 0.5
+
+
+def test_rescale_overlap_uses_whole_ball_statistics():
+    u = np.array([0.05, 0.4, 0.5, 0.35, 0.1, 0.9, 0.6, 0.7, 0.5, 0.8])[None, None, None]
+    seeds = [(2, 0, 0, 0), (7, 0, 0, 0)]
+    out = O.rescale(u, seeds, r=3.0).reshape(-1)
+    x = u.reshape(-1)
+    # ball 0: mu 0.05 (voxel 0), xi 0.9 (voxel 5, owned by seed 1)
+    # ball 1: mu 0.1 (voxel 4, owned by seed 0), xi 0.9 (voxel 5)
+    expect = np.concatenate([(x[:5] - 0.05) / 0.85, (x[5:] - 0.1) / 0.8])
+    np.testing.assert_allclose(out, expect, rtol=1e-15, atol=0)
+    # so seed 0's owned voxels do not reach 1, and seed 1's do not reach 0
+    assert out[:5].max() < 0.6 and out[5:].min() > 0.4
