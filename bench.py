@@ -1,16 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the 4D GSUBSURF segmentation hot path on GB300.
 
-One bench step = one whole segmentation of the medium synthetic workload
-(128x128x64 space x 32 frames = 33.5M voxels, 60 nuclei, 50 semi-implicit
-steps): set-up (thresholding, two presmoothing solves, face coefficients, u0)
-and 50 x {coefficients, red-black SOR solve to the stopping rule, rescale},
-all through the C ABI with the image already resident in HBM.
+One bench step = one whole segmentation of the large synthetic workload
+(512x512x128 space x 48 frames = 1.61G voxels, one nucleus per 40^3 voxels,
+20 semi-implicit steps), with the image already resident in HBM: set-up
+(thresholding, two presmoothing solves, face coefficients, u0) and
+20 x {coefficients, red-black SOR solve to the stopping rule, rescale}, all
+through the C ABI.
 
 metric: voxel-sweeps/s = voxels x red-black sweeps (every solve, set-up
 included) / wall time of the whole segmentation.  The roofline object is for
 the dominant kernel (the red-black half sweep): algorithmic bytes per launch /
 its CUDA-event time on the launching stream, against the measured HBM peak.
+
+Further legs: the medium workload (128x128x64 x 32 frames, 50 steps) in FP32
+and in mixed precision, a grid of the paper's largest stack on a lean handle,
+the batched per-nucleus windows, and serving.
 
 --impl reference times the FP64 CPU oracle (the reference of this project) on
 a bounded crop of the same workload.  Multi-GPU (torchrun): independent
@@ -19,8 +24,10 @@ replicas, one per GPU (the full-grid path does not shard: replicas only).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -30,14 +37,46 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ALG_BYTES_PER_VOXEL_SWEEP = 32.0   # u r/w 8 + beta/gamma 8 + 4 FP32 face weights 16
+# Algorithmic bytes per voxel-sweep of the sweep as launched: the FP32 solve
+# sweeps its correction system in symmetrically scaled form, reading the
+# correction (r + w 8), its right-hand side (4) and four FP32 face weights
+# per voxel (16); the lean handle's unscaled sweep also reads gamma = c/D (4).
+ALG_BYTES_SCALED = 28.0
+ALG_BYTES_UNSCALED = 32.0
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes (read + write) per full sweep of the medium grid, from one ncu
-# capture of the current kernel (profiles/); None after a kernel changes until
-# it is captured again.
 SWEEP_KERNELS = {0: "k_sweep_wave (fused frame pipeline, several sweeps per launch)",
                  1: "k_sweep_vec (one colour of a red-black sweep per launch, 2 voxels/thread)"}
-SWEEP_TRAFFIC_PER_SWEEP = {0: (12189379840 + 1330637312) / 10, 1: (731106816 + 61575168) + (731059968 + 61712640)}
+# DRAM traffic of the sweep comes from a committed ncu summary: its
+# "bench-record:" line gives the bytes per voxel update and the hash of the
+# kernel sources at capture time; a record whose hash differs from the
+# current sources is stale and gives no traffic figure.
+SWEEP_SOURCES = ["solve_kernels.cu", "stencil.cuh", "seg4d_internal.cuh"]
+
+
+def sweep_src_sha():
+    h = hashlib.sha256()
+    for name in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2111_11866_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def sweep_traffic_record(profile):
+    """(bytes per voxel update, record) from profiles/<profile>, or (None,
+    reason) when the record is missing or was taken on other sources."""
+    path = os.path.join(ROOT, "profiles", profile)
+    try:
+        with open(path) as fh:
+            text = fh.read()
+    except OSError:
+        return None, f"no {profile}"
+    m = re.search(r"bench-record: kernel=(\S+) src_sha=(\S+) bytes_per_voxel_update=([0-9.]+)",
+                  text)
+    if not m:
+        return None, f"no bench-record line in {profile}"
+    if m.group(2) != sweep_src_sha():
+        return None, f"{profile}: captured on other kernel sources (src_sha {m.group(2)})"
+    return float(m.group(3)), f"{profile} ({m.group(1)}, src_sha {m.group(2)})"
 
 
 def _env_int(name, default):
@@ -132,13 +171,49 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def _crop_case(case, n=(64, 64, 32, 8)):
+CROP = (64, 64, 32, 8)   # (n1, n2, n3, n4) of the CPU baselines' sample
+
+
+def _crop_box(seeds, dims, n=CROP):
+    """Origin of an n-sized box around the seed nearest the grid centre."""
     import numpy as np
+    c = np.array(dims[:3], float) / 2
+    s = seeds[np.argmin(((seeds[:, :3] - c) ** 2).sum(1))]
+    return [int(min(max(0, round(s[d]) - n[d] // 2), dims[d] - n[d])) for d in range(3)]
+
+
+def _crop_seeds(seeds, org, n=CROP):
+    import numpy as np
+    sh = seeds.copy()
+    sh[:, :3] -= np.array(org, float)
+    keep = ((sh[:, 0] >= 0) & (sh[:, 0] < n[0]) & (sh[:, 1] >= 0) & (sh[:, 1] < n[1]) &
+            (sh[:, 2] >= 0) & (sh[:, 2] < n[2]) & (sh[:, 3] < n[3]))
+    return sh[keep]
+
+
+def large_crop(img=None, frames=48, n=CROP):
+    """The CPU baselines' sample of the large workload: an n-sized crop (first
+    n4 frames) around the nucleus nearest the grid centre.  From the device
+    image when given, else the first n4 frames generated on the host by the
+    same seeded generator.  Returns (image (n4, n3, n2, n1) numpy, seeds,
+    description)."""
+    import numpy as np
+    from paper_2111_11866_gb300 import synth
+    dims = (512, 512, 128, frames)
+    seeds, count, gen = synth.nuclei_frames(3, dims, 1.0 / 40 ** 3, "cpu" if img is None else
+                                            img.device)
+    x0, y0, z0 = _crop_box(seeds, dims, n)
     n1, n2, n3, n4 = n
-    img = case.image[:n4, :n3, :n2, :n1].copy()
-    s = case.seeds
-    keep = (s[:, 0] < n1) & (s[:, 1] < n2) & (s[:, 2] < n3) & (s[:, 3] < n4)
-    return img, s[keep]
+    if img is not None:
+        crop = img[:n4, z0:z0 + n3, y0:y0 + n2, x0:x0 + n1].cpu().numpy().copy()
+    else:
+        crop = np.empty((n4, n3, n2, n1), np.float32)
+        for l, f in enumerate(gen):
+            crop[l] = f[z0:z0 + n3, y0:y0 + n2, x0:x0 + n1].numpy()
+            if l + 1 == n4:
+                break
+    desc = f"{n1}x{n2}x{n3}x{n4} crop at ({x0},{y0},{z0},0) of the large 512x512x128x{frames} grid"
+    return crop, _crop_seeds(seeds, (x0, y0, z0), n), desc
 
 
 def _host_cpu():
@@ -158,13 +233,12 @@ def _host_cpu():
     return {"nproc": os.cpu_count(), "machine": platform.machine(), "model": model}
 
 
-def oracle_sample(case, params, nsteps=1, omp=False):
+def oracle_sample(img, seeds, where, params, nsteps=2, omp=False):
     """The FP64 oracle, as it stands, on a crop of the workload: returns
-    (voxel-sweeps per second, description, seconds).  omp: its OpenMP build
-    (the paper's frame-split red-black sweeps on all host cores)."""
+    (voxel-sweeps per second, description, seconds, threads).  omp: its OpenMP
+    build (the paper's frame-split red-black sweeps on all host cores)."""
     import numpy as np
     import oracle as O
-    img, seeds = _crop_case(case)
     P = O.OracleParams(h=tuple(params.h), tau=params.tau, eps=params.eps, K=params.K,
                        delta=params.delta, vartheta=params.vartheta, lambda_th=params.lambda_th,
                        r_ball=params.r_ball, R_init=params.R_init, v_init=params.v_init,
@@ -172,39 +246,40 @@ def oracle_sample(case, params, nsteps=1, omp=False):
     t0 = time.perf_counter()
     u, info = O.segment(img.astype(np.float64), seeds, P, nsteps=nsteps, omp=omp)
     dt = time.perf_counter() - t0
-    nv = img.size
     sweeps = sum(info["iters"])
     how = (f"OpenMP build, {O.threads(True)} threads, frame-split red-black sweeps" if omp
            else "1 thread")
-    desc = (f"oracle (plain C, FP64, {how}) full pipeline on a {img.shape[3]}x{img.shape[2]}x"
-            f"{img.shape[1]}x{img.shape[0]} crop of the workload ({len(seeds)} seeds), {nsteps} "
-            f"step(s) solved to 1e-12; counts step-solve sweeps, times set-up too")
-    return nv * sweeps / dt, desc, dt, (O.threads(True) if omp else 1)
+    desc = (f"oracle (plain C, FP64, {how}) full pipeline on a {where} ({len(seeds)} seeds), "
+            f"{nsteps} step(s) solved to 1e-12; counts step-solve sweeps, times set-up too")
+    return img.size * sweeps / dt, desc, dt, (O.threads(True) if omp else 1)
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, each step a
+    bounded sample (a crop, one time step) of the large workload."""
     if rank != 0:
         return
-    from paper_2111_11866_gb300 import synth
     from paper_2111_11866_gb300._lib import Params
     import oracle
     oracle.build()
-    case = synth.medium()
+    img, seeds, where = large_crop()
     params = Params()
     for _ in range(args.warmup):
-        oracle_sample(case, params)
+        oracle_sample(img, seeds, where, params)
     vals, times = [], []
     desc = ""
     for _ in range(args.steps):
-        v, desc, dt, _ = oracle_sample(case, params)
+        v, desc, dt, _ = oracle_sample(img, seeds, where, params)
         vals.append(v)
         times.append(dt)
     value = statistics.mean(vals)
+    cfg = _config_large()
+    cfg["sample"] = f"each step: {where}, 2 time steps (the full workload takes the oracle days)"
     line = {"impl": "reference", "metric": "voxel-sweeps/s", "value": value,
             "unit": "voxel-sweeps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": _config(case),
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": "voxel-sweeps/s", "cores": 1,
                              "kind": "oracle", "sample": desc, "host": _host_cpu()},
             "e2e": {"value": value, "unit": "voxel-sweeps/s", "h2d_bytes_per_step": 0,
@@ -212,12 +287,12 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def _config(case):
-    n1, n2, n3, n4 = case.dims
-    return {"workload": f"medium full grid {n1}x{n2}x{n3}x{n4}, {case.meta['count']} nuclei, "
-                        f"{case.nsteps} steps", "n1": n1, "n2": n2, "n3": n3, "n4": n4,
-            "voxels": n1 * n2 * n3 * n4, "time_steps": case.nsteps,
-            "parallelism": "replicas", "l2": "inputs larger than L2 (about 3 GB resident)"}
+def _config_large(frames=48, nsteps=20):
+    return {"workload": f"large full grid 512x512x128x{frames}, 1 nucleus per 40^3 voxels, "
+                        f"{nsteps} steps", "n1": 512, "n2": 512, "n3": 128, "n4": frames,
+            "voxels": 512 * 512 * 128 * frames, "time_steps": nsteps,
+            "parallelism": "replicas",
+            "l2": "inputs larger than L2 (about 200 GB resident)"}
 
 
 def _plain_window(img_d, seeds, nsteps, params):
@@ -241,58 +316,184 @@ def _mixed(params):
     return pm
 
 
-def run_large(nsteps, params, local, frames=48):
-    """The large full grid (512x512x128 x 48 frames, 1.61G voxels, one nucleus
-    per 40^3 voxels), built on the device, `nsteps` time steps after the
-    set-up; whole-step voxel-sweeps/s, the sweep kernel's rate and its
-    roofline fraction (algorithmic bytes, CUDA-event time)."""
+def _roofline(nvox, sweeps, sweep_ms, sweep_launches, alg_bytes, kernel, traffic_rec=None):
+    """Roofline of the sweep: algorithmic bytes of one launch (alg_bytes per
+    voxel-sweep x the voxel-sweeps of a launch) / the launch's average
+    CUDA-event time, against the measured HBM peak; traffic = DRAM bytes of
+    one launch from the committed capture record, when it is current."""
+    peak, peak_kind = _peaks()
+    per_launch_sweeps = sweeps / max(sweep_launches, 1)
+    per_launch_bytes = alg_bytes * nvox * per_launch_sweeps
+    launch_ms = sweep_ms / max(sweep_launches, 1)
+    achieved = per_launch_bytes / (launch_ms / 1000.0) / 1e9 if launch_ms > 0 else None
+    out = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak if achieved else None, "traffic": None,
+           "peak_kind": peak_kind, "alg_bytes_per_voxel_sweep": alg_bytes,
+           "alg_bytes_per_launch": per_launch_bytes, "sweeps_per_launch": per_launch_sweeps,
+           "avg_launch_ms": launch_ms}
+    if traffic_rec is not None:
+        b_upd, src = traffic_rec
+        out["traffic_source"] = src
+        if b_upd is not None:
+            # a launch updates the voxels of one colour: per_launch_sweeps x nvox updates x 2
+            out["traffic"] = b_upd * nvox * per_launch_sweeps * 2.0
+            out["traffic_bytes_per_voxel_update"] = b_upd
+    return out
+
+
+def run_headline(args, params, local, dist, world):
+    """The large workload (512x512x128 x 48 frames, 1.61G voxels, 20 steps),
+    built on the device: W warm-up and K timed whole segmentations with the
+    image resident in HBM, then the same through the ABI from pinned host
+    memory with u read back (e2e), and the CPU baselines on a crop."""
+    import numpy as np
     import torch
     from paper_2111_11866_gb300 import _lib, synth
 
-    img, seeds, _, meta = synth.large("cuda", frames=frames)
-    dims = tuple(reversed(img.shape))
-    nvox = img.numel()
+    img_d, seeds, nsteps, meta = synth.large("cuda", frames=args.large_frames)
+    if args.time_steps is not None:
+        nsteps = args.time_steps
+    dims = tuple(reversed(img_d.shape))
+    nvox = img_d.numel()
+    crop = large_crop(img_d, frames=args.large_frames)   # CPU baselines' sample
     torch.cuda.synchronize()
-    torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
     seg = _lib.Seg4D(dims, stream=stream, params=params)
-    try:
-        seg.set_image(img)
-        del img
-        torch.cuda.empty_cache()
+
+    def one_step(src):
+        seg.set_image(src)
         seg.set_seeds(seeds)
-        t_setup = time.perf_counter()
-        seg.setup()
+        return seg.step(nsteps)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
         torch.cuda.synchronize()
-        t_setup = time.perf_counter() - t_setup
+
+    try:
+        for _ in range(max(args.warmup, 0)):
+            one_step(img_d)
         sampler = ClockSampler(local)
+        barrier()
         sampler.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        sweeps = launches = sweep_launches = 0
+        sweep_ms = 0.0
+        infos = []
         e0.record(stream)
-        info = seg.step(nsteps)
+        for _ in range(args.steps):
+            info = one_step(img_d)
+            infos.append(info)
+            sweeps += info["sweeps_total"]
+            sweep_ms += info["sweep_ms"]
+            sweep_launches += info["sweep_launches"]
+            launches += info["launches"] + 1      # + the image split kernel of set_image
         e1.record(stream)
-        torch.cuda.synchronize()
+        barrier()
         clocks = sampler.stop()
-        ms = e0.elapsed_time(e1)
-        sweeps = info["sweeps_total"]
-        peak, peak_kind = _peaks()
-        rate = nvox * sweeps / (info["sweep_ms"] / 1000.0)
-        return {"workload": f"{meta['name']} ({meta['count']} nuclei), {nsteps} steps",
-                "voxels": nvox, "value": nvox * sweeps / (ms / 1000.0),
-                "unit": "voxel-sweeps/s", "ms_per_time_step": ms / nsteps,
-                "sweeps_per_time_step": sweeps / nsteps, "sweep_rate": rate,
-                "roofline": {"bound": "hbm", "kernel": SWEEP_KERNELS[params.sweep_variant],
-                             "achieved": ALG_BYTES_PER_VOXEL_SWEEP * rate / 1e9, "peak": peak,
-                             "unit": "GB/s",
-                             "frac": ALG_BYTES_PER_VOXEL_SWEEP * rate / 1e9 / peak,
-                             "peak_kind": peak_kind},
-                "last_res_rel": info["res_rel"], "setup_s": t_setup,
-                "device_gb": _lib.Seg4D.device_bytes(dims) / 1e9, "clocks": clocks,
-                "data": "synthetic, generated on the device (seeded)"}
+        elapsed_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        value = job_rate(world, nvox * sweeps, elapsed_ms / 1000.0)
+
+        # end to end through the same ABI with host buffers: the image comes
+        # from pinned host memory and u goes back to it, copies timed
+        img_h = torch.empty(img_d.shape, dtype=torch.float32, pin_memory=True)
+        img_h.copy_(img_d)
+        out_h = torch.empty(img_d.shape, dtype=torch.float32, pin_memory=True)
+        del img_d
+        torch.cuda.empty_cache()
+        barrier()
+        t0 = time.perf_counter()
+        e2e_sweeps = 0
+        e2e_steps = 1
+        for _ in range(e2e_steps):
+            info = one_step(img_h)
+            e2e_sweeps += info["sweeps_total"]
+            seg.read_u(out_h)
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": job_rate(world, nvox * e2e_sweeps, e2e_s), "unit": "voxel-sweeps/s",
+               "h2d_bytes_per_step": img_h.nbytes, "d2h_bytes_per_step": out_h.nbytes,
+               "steps": e2e_steps}
+        last = infos[-1]
+        res = {"value": value, "elapsed_ms": elapsed_ms, "nvox": nvox, "sweeps": sweeps,
+               "launches": launches, "clocks": clocks, "e2e": e2e, "crop": crop,
+               "config": _config_large(args.large_frames, nsteps), "meta": meta,
+               "sweep_rate": nvox * sweeps / (sweep_ms / 1000.0) if sweep_ms > 0 else None,
+               "roofline": _roofline(nvox, sweeps, sweep_ms, sweep_launches, ALG_BYTES_SCALED,
+                                     SWEEP_KERNELS[params.sweep_variant],
+                                     sweep_traffic_record("k_sweep_vec_large_planes.md")),
+               "sweeps_per_segmentation": sweeps / args.steps,
+               "ms_per_time_step": elapsed_ms / args.steps / nsteps,
+               "last_solve": {"res_rel": last["res_rel"],
+                              "res_inf_rel": last["res_inf"] / max(last["bmax"], 1e-300)},
+               "device_gb": _lib.Seg4D.device_bytes(dims) / 1e9}
+        return res
     finally:
         seg.close()
         torch.cuda.empty_cache()
+
+
+def run_medium(args, params, local):
+    """The medium workload (128x128x64 x 32 frames, 33.5M voxels, 50 steps):
+    whole segmentations in FP32 and in mixed precision on one handle, the
+    image resident in HBM, with the sweep's roofline and the mixed result's
+    difference from the FP32 one."""
+    import numpy as np
+    import torch
+    from paper_2111_11866_gb300 import _lib, synth
+
+    case = synth.medium()
+    nvox = int(np.prod(case.dims))
+    stream = torch.cuda.current_stream()
+    img_d = torch.from_numpy(case.image).cuda()
+    out = {"workload": f"medium full grid 128x128x64x32, {case.meta['count']} nuclei, "
+                       f"{case.nsteps} steps", "voxels": nvox}
+    with _lib.Seg4D(case.dims, stream=stream, params=params) as seg:
+        def run(k):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            sw = sl = 0
+            sms = 0.0
+            e0.record(stream)
+            for _ in range(k):
+                seg.set_image(img_d)
+                seg.set_seeds(case.seeds)
+                info = seg.step(case.nsteps)
+                sw += info["sweeps_total"]
+                sms += info["sweep_ms"]
+                sl += info["sweep_launches"]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), sw, sms, sl, info
+
+        run(1)
+        ms, sw, sms, sl, info = run(args.medium_steps)
+        out.update({"value": nvox * sw / (ms / 1000.0), "unit": "voxel-sweeps/s",
+                    "ms_per_segmentation": ms / args.medium_steps,
+                    "sweeps_per_segmentation": sw / args.medium_steps,
+                    "sweep_rate": nvox * sw / (sms / 1000.0),
+                    "roofline": _roofline(nvox, sw, sms, sl, ALG_BYTES_SCALED,
+                                          SWEEP_KERNELS[params.sweep_variant],
+                                          sweep_traffic_record("k_sweep_vec_medium.md"))})
+        u_plain = seg.read_u()
+        if args.mixed_steps > 0:
+            seg.set_params(precision=1)
+            run(1)
+            ms, sw, sms, sl, info = run(args.mixed_steps)
+            u_mixed = seg.read_u()
+            seg.set_params(precision=0)
+            out["mixed_precision"] = {
+                "value": nvox * sw / (ms / 1000.0), "unit": "voxel-sweeps/s",
+                "ms_per_segmentation": ms / args.mixed_steps,
+                "sweeps_per_segmentation": sw / args.mixed_steps,
+                "sweep_rate": nvox * sw / (sms / 1000.0),
+                "max_rel_diff_vs_f32": float(np.abs(u_mixed - u_plain).max() /
+                                             max(np.abs(u_plain).max(), 1e-30)),
+                "dtype": "bf16 sweep weights, f32 sweeps and defect passes, f64 norms"}
+    del img_d
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_paper_scale(nsteps, params, local):
@@ -342,7 +543,8 @@ def run_paper_scale(nsteps, params, local):
                 "value": nvox * sweeps / (ms / 1000.0), "unit": "voxel-sweeps/s",
                 "ms_per_time_step": ms / nsteps, "sweeps_per_time_step": sweeps / nsteps,
                 "sweep_rate": rate,
-                "roofline_frac": ALG_BYTES_PER_VOXEL_SWEEP * rate / 1e9 / peak,
+                "roofline_frac": ALG_BYTES_UNSCALED * rate / 1e9 / peak,
+                "alg_bytes_per_voxel_sweep": ALG_BYTES_UNSCALED,
                 "peak_kind": peak_kind, "last_res_rel": info["res_rel"],
                 "u_range": [info["umin"], info["umax"]], "setup_s": t_setup,
                 "setup_sweeps": info0["sweeps_total"], "generate_s": t_gen, "clocks": clocks,
@@ -456,30 +658,30 @@ def run_serving(rate, seconds, budget_gb, params, pool=24):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=3,
+                    help="timed whole segmentations of the large workload")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batched-windows", type=int, default=128,
-                    help="per-nucleus windows of the batched measurement (0 = skip; 4096 = "
-                         "the full batched workload)")
+    ap.add_argument("--large-frames", type=int, default=48,
+                    help="frames of the large grid (fewer: the same planes, for profiling)")
+    ap.add_argument("--time-steps", type=int, default=None,
+                    help="override the large workload's 20 time steps (profiling runs only)")
+    ap.add_argument("--medium-steps", type=int, default=3,
+                    help="timed segmentations of the medium workload (0 = skip)")
+    ap.add_argument("--mixed-steps", type=int, default=3,
+                    help="segmentations of the medium workload in mixed precision (0 = skip)")
+    ap.add_argument("--paper-steps", type=int, default=5,
+                    help="time steps of the 567x577x147x70 grid with a lean handle (0 = skip)")
+    ap.add_argument("--batched-windows", type=int, default=4096,
+                    help="per-nucleus windows of the batched measurement (0 = skip)")
     ap.add_argument("--batched-steps", type=int, default=30)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests/s")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="arrival horizon of the serving measurement (0 = skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
-    ap.add_argument("--paper-steps", type=int, default=0,
-                    help="time steps of the 567x577x147x70 grid with a lean handle (0 = skip)")
-    ap.add_argument("--mixed-steps", type=int, default=2,
-                    help="segmentations of the mixed-precision measurement (0 = skip)")
-    ap.add_argument("--large-steps", type=int, default=20,
-                    help="time steps of the large 512x512x128x48 grid (0 = skip)")
-    ap.add_argument("--large-frames", type=int, default=48,
-                    help="frames of the large grid (fewer: the same planes, for profiling)")
     ap.add_argument("--sweep-variant", type=int, default=1, choices=[0, 1],
                     help="0 = fused frame-pipeline sweep, 1 = one launch per colour")
-    ap.add_argument("--time-steps", type=int, default=None,
-                    help="override the workload's 50 time steps (profiling runs only)")
     args = ap.parse_args()
 
     rank = _env_int("RANK", 0)
@@ -490,7 +692,6 @@ def main():
         run_reference(args, rank, world)
         return
 
-    import numpy as np
     import torch
 
     dist = None
@@ -501,125 +702,28 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2111_11866_gb300 import _lib, synth
+    from paper_2111_11866_gb300 import _lib
 
-    case = synth.medium()
-    if args.time_steps is not None:
-        case.nsteps = args.time_steps
-    n1, n2, n3, n4 = case.dims
-    nvox = n1 * n2 * n3 * n4
     params = _lib.Params.defaults()
     params.sweep_variant = args.sweep_variant
-    stream = torch.cuda.current_stream()
-    img_d = torch.from_numpy(case.image).cuda()
-    seg = _lib.Seg4D(case.dims, stream=stream, params=params)
-
-    def one_step():
-        seg.set_image(img_d)
-        seg.set_seeds(case.seeds)
-        return seg.step(case.nsteps)
-
-    for _ in range(max(args.warmup, 0)):
-        one_step()
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    sampler = ClockSampler(local)
-    barrier()
-    sampler.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    sweeps = 0
-    sweep_ms = 0.0
-    launches = 0
-    sweep_launches = 0
-    e0.record(stream)
-    for _ in range(args.steps):
-        info = one_step()
-        sweeps += info["sweeps_total"]
-        sweep_ms += info["sweep_ms"]
-        sweep_launches += info["sweep_launches"]
-        launches += info["launches"] + 1          # + the image split kernel of set_image
-    e1.record(stream)
-    barrier()
-    clocks = sampler.stop()
-    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-    value = job_rate(world, nvox * sweeps, elapsed_ms / 1000.0)
-
-    # end to end through the same ABI with host buffers and copies in the timed
-    # region: the image comes from pinned host memory and u goes back to it
-    img_h = torch.from_numpy(np.ascontiguousarray(case.image)).pin_memory()
-    out_h = torch.empty(img_h.shape, dtype=torch.float32, pin_memory=True)
-    e2e_steps = max(1, min(args.steps, 2))
-    barrier()
-    t0 = time.perf_counter()
-    e2e_sweeps = 0
-    for _ in range(e2e_steps):
-        seg.set_image(img_h)
-        seg.set_seeds(case.seeds)
-        info = seg.step(case.nsteps)
-        e2e_sweeps += info["sweeps_total"]
-        seg.read_u(out_h)
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
-    e2e_value = job_rate(world, nvox * e2e_sweeps, e2e_s)
-
-    # roofline of the dominant kernel (the sweep): algorithmic bytes of the
-    # sweeps one launch performs / the launch's CUDA-event time
-    peak, peak_kind = _peaks()
-    sweeps_per_launch = sweeps / max(sweep_launches, 1)
-    per_launch_bytes = ALG_BYTES_PER_VOXEL_SWEEP * nvox * sweeps_per_launch
-    launch_ms = sweep_ms / max(sweep_launches, 1)
-    achieved = per_launch_bytes / (launch_ms / 1000.0) / 1e9 if launch_ms > 0 else None
-    kernel_name = SWEEP_KERNELS[params.sweep_variant]
-
-    # the same workload in mixed precision (same handle, same inputs)
-    mixed = None
-    nm = min(args.steps, args.mixed_steps)
-    if nm > 0:
-        u_plain = seg.read_u()
-        seg.set_params(precision=1)
-        one_step()
-        mixed_sweeps = 0
-        mixed_sweep_ms = 0.0
-        e0.record(stream)
-        for _ in range(nm):
-            info = one_step()
-            mixed_sweeps += info["sweeps_total"]
-            mixed_sweep_ms += info["sweep_ms"]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        mixed_ms = e0.elapsed_time(e1)
-        u_mixed = seg.read_u()
-        seg.set_params(precision=0)
-        mixed = {"value": nvox * mixed_sweeps / (mixed_ms / 1000.0), "unit": "voxel-sweeps/s",
-                 "ms_per_step": mixed_ms / nm, "sweeps_per_segmentation": mixed_sweeps / nm,
-                 "sweep_rate": nvox * mixed_sweeps / (mixed_sweep_ms / 1000.0),
-                 "max_rel_diff_vs_f32": float(np.abs(u_mixed - u_plain).max() /
-                                              max(np.abs(u_plain).max(), 1e-30)),
-                 "dtype": "bf16 sweep weights, f32 sweeps and defect passes, f64 norms"}
+    head = run_headline(args, params, local, dist, world)
 
     cpu = cpu_omp = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, _, _ = oracle_sample(case, params)
+        img, seeds, where = head["crop"]
+        v, desc, _, _ = oracle_sample(img, seeds, where, params)
         cpu = {"value": v, "unit": "voxel-sweeps/s", "cores": 1, "kind": "oracle", "sample": desc,
                "host": _host_cpu()}
         try:
-            v, desc, _, cores = oracle_sample(case, params, omp=True)
+            v, desc, _, cores = oracle_sample(img, seeds, where, params, omp=True)
             cpu_omp = {"value": v, "unit": "voxel-sweeps/s", "cores": cores,
                        "kind": "oracle, OpenMP build", "sample": desc}
         except Exception as e:   # noqa: BLE001 -- no OpenMP toolchain on the host
             cpu_omp = {"unavailable": f"OpenMP build of the oracle failed: {e}"[:200]}
 
-    seg.close()
-    del img_d
-    torch.cuda.empty_cache()
-    batched = serving = large = paper = None
-    if args.large_steps > 0:
-        large = run_large(args.large_steps, params, local, frames=args.large_frames)
+    medium = paper = batched = serving = None
+    if args.medium_steps > 0:
+        medium = run_medium(args, params, local)
     if args.paper_steps > 0:
         paper = run_paper_scale(args.paper_steps, params, local)
     if args.batched_windows > 0:
@@ -629,31 +733,23 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "voxel-sweeps/s", "value": value, "unit": "voxel-sweeps/s",
+            "metric": "voxel-sweeps/s", "value": head["value"], "unit": "voxel-sweeps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "ms_per_step": head["elapsed_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(case),
-            "sweeps_per_segmentation": sweeps / args.steps,
-            "sweep_rate": nvox * sweeps / (sweep_ms / 1000.0) if sweep_ms > 0 else None,
-            "roofline": {"bound": "hbm", "kernel": kernel_name,
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak if achieved else None,
-                         "traffic": (SWEEP_TRAFFIC_PER_SWEEP[params.sweep_variant] *
-                                     sweeps_per_launch
-                                     if SWEEP_TRAFFIC_PER_SWEEP[params.sweep_variant] else None),
-                         "peak_kind": peak_kind,
-                         "alg_bytes_per_launch": per_launch_bytes,
-                         "sweeps_per_launch": sweeps_per_launch,
-                         "avg_launch_ms": launch_ms},
+            "config": head["config"],
+            "sweeps_per_segmentation": head["sweeps_per_segmentation"],
+            "ms_per_time_step": head["ms_per_time_step"],
+            "sweep_rate": head["sweep_rate"],
+            "roofline": head["roofline"],
+            "last_solve": head["last_solve"],
+            "device_gb": head["device_gb"],
             "cpu_baseline": cpu,
             "cpu_baseline_omp": cpu_omp,
-            "e2e": {"value": e2e_value, "unit": "voxel-sweeps/s",
-                    "h2d_bytes_per_step": img_h.nbytes, "d2h_bytes_per_step": out_h.nbytes},
-            "gpu_launches": launches,
-            "clocks": clocks,
-            "mixed_precision": mixed,
-            "large": large,
+            "e2e": head["e2e"],
+            "gpu_launches": head["launches"],
+            "clocks": head["clocks"],
+            "medium": medium,
             "paper_scale": paper,
             "batched": batched,
             "serving": serving,

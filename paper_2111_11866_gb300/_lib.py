@@ -46,7 +46,8 @@ class CParams(C.Structure):
                 ("v_init", C.c_double), ("sigma_t", C.c_double), ("omega", C.c_double),
                 ("omega_smooth", C.c_double), ("tol", C.c_double), ("tol_smooth", C.c_double),
                 ("max_iters", C.c_int), ("check_every", C.c_int), ("precision", C.c_int),
-                ("sweep_variant", C.c_int), ("ctas_per_sm", C.c_int), ("wait_test", C.c_int)]
+                ("sweep_variant", C.c_int), ("ctas_per_sm", C.c_int), ("wait_test", C.c_int),
+                ("tol_inf", C.c_double)]
 
 
 class CSeed(C.Structure):
@@ -59,7 +60,7 @@ class CInfo(C.Structure):
                 ("res_rel", C.c_double), ("bnorm", C.c_double), ("umin", C.c_double),
                 ("umax", C.c_double), ("sweeps_total", C.c_longlong), ("steps_done", C.c_int),
                 ("ms", C.c_float), ("sweep_ms", C.c_double), ("launches", C.c_longlong),
-                ("sweep_launches", C.c_longlong)]
+                ("sweep_launches", C.c_longlong), ("res_inf", C.c_double), ("bmax", C.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -146,6 +147,7 @@ class Params:
     sweep_variant: int = 1
     ctas_per_sm: int = 0
     wait_test: int = 0
+    tol_inf: float = 1e-5
 
     @classmethod
     def defaults(cls) -> "Params":

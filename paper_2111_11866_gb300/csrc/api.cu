@@ -31,6 +31,31 @@ int next_check_batch(double rn, double prev_rn, int it, int prev_it, double tol,
                                : check_every;
 }
 
+int check_decision(CheckState &cs, double rn, double bn, double rinf, double bmax, int it,
+                   double tol, double tol_inf, int check_every, bool mixed, int &batch)
+{
+    const bool l2 = rn <= tol * bn;
+    const bool inf = tol_inf <= 0.0 || rinf <= tol_inf * bmax;
+    int res = kGoOn;
+    if (l2 && inf) {
+        res = kStop;
+    } else if (l2 && cs.prev_inf > 0.0 && it - cs.prev_it >= check_every) {
+        const double rho = std::pow(rinf / cs.prev_inf, 1.0 / (it - cs.prev_it));
+        if (!(rho < 0.99)) res = kStopFloor;
+    }
+    if (res == kGoOn) {
+        if (l2)
+            batch = std::max(check_every, next_check_batch(rinf, cs.prev_inf, it, cs.prev_it,
+                                                           tol_inf, bmax, check_every, mixed));
+        else
+            batch = next_check_batch(rn, cs.prev_rn, it, cs.prev_it, tol, bn, check_every, mixed);
+    }
+    cs.prev_rn = rn;
+    cs.prev_inf = rinf;
+    cs.prev_it = it;
+    return res;
+}
+
 // message of the last failed handle-free call of this thread (seg4d_create,
 // seg4d_residual_norms_noalloc), reported by seg4d_last_error(NULL)
 std::string &handle_free_error()
@@ -166,7 +191,7 @@ size_t bytes_for(const Layout &L, long long nv, bool lean = false)
         // u, beta, gamma, diag, W, G, owner, ib, rho, dlt (see seg4d_create_ex)
         const size_t S = (size_t)L.S;
         return 2 * S * 4 * 4 + 8 * S * 4 + 16 * S * 4 + 2 * S * 4 + 3 * 2 * S * 4 +
-               3 * kPartCap * sizeof(double) + 8 * sizeof(double);
+               4 * kPartCap * sizeof(double) + 8 * sizeof(double);
     }
     const size_t S = (size_t)L.S;
     size_t b = 0;
@@ -176,7 +201,7 @@ size_t bytes_for(const Layout &L, long long nv, bool lean = false)
     b += 2 * S * sizeof(float) * 4;        // I0, ITH, Is0, IsTH
     b += 2 * S * sizeof(int);              // owner
     b += (size_t)nv * sizeof(float);       // staging
-    b += 3 * kPartCap * sizeof(double) + 8 * sizeof(double);
+    b += 4 * kPartCap * sizeof(double) + 8 * sizeof(double);
     b += 8 * S * sizeof(float) + 2 * S * sizeof(float) * 4;   // FP32 solve: Ws, rs, ib, rho, dlt
     return b;
 }
@@ -233,10 +258,12 @@ seg4d_status use_device(seg4d *h)
     return SEG4D_OK;
 }
 
-// reduce the per-block records into scal[slot..slot+2]
-seg4d_status reduce_into(seg4d *h, int slot, int nrec = kPartBlocks)
+// reduce the per-block records into scal[slot..slot+2]; with_max: also the
+// defect pass's per-block max |r| into scal[slot+3]
+seg4d_status reduce_into(seg4d *h, int slot, int nrec = kPartBlocks, bool with_max = false)
 {
-    launch_reduce_partials(h->partials, nrec, h->scal + slot, h->stream);
+    launch_reduce_partials(h->partials, nrec, h->scal + slot, h->stream,
+                           with_max ? h->partials + 3 * kPartCap : nullptr);
     h->launches += 1;
     CK_LAUNCH("reduce");
     return SEG4D_OK;
@@ -253,6 +280,7 @@ seg4d_status fetch_scal(seg4d *h)
 struct SolveOut {
     int iters = 0;
     double res = 0, bnorm = 0, umin = 0, umax = 0;
+    double res_inf = 0, bmax = 0;   // max |r| and max |b|
     bool converged = false;
 };
 
@@ -295,10 +323,15 @@ seg4d_status ensure_solve_arrays(seg4d *h, bool mixed)
 // (Ws, r; see k_scaled_weights), u += r delta.  Mixed (precision 1): BF16
 // weights with the consistent diagonal D_b, u += delta.  The brec per-block
 // records of ||b||^2 must be in `partials` (written by the coefficient
-// kernel).  Stopping rule: ||b - A u||_2 <= tol ||b||_2, tested before the
-// first sweep and then at the spacing of next_check_batch.
+// kernel).  Stopping rule: ||b - A u||_2 <= tol ||b||_2 and, with tol_inf >
+// 0, also max |b - A u| <= tol_inf max |b| -- a per-voxel bound, since the
+// M-matrix of the Theorem in Section 3.3 has ||A^-1||_inf <= 1, so each
+// voxel of the solve is within max |r| of the exact solution.  Tested before
+// the first sweep and then at the spacing check_decision picks (which also
+// ends a solve whose max |r| has reached its FP32 floor).
 seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol, int max_iters,
-                          int check_every, SolveOut &out, bool mixed = false)
+                          int check_every, SolveOut &out, bool mixed = false,
+                          double tol_inf = 0.0)
 {
     const Layout &L = h->L;
     seg4d_status st = reduce_into(h, 0, brec);   // scal[0..2] = sum b^2, min b, max b
@@ -319,15 +352,16 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
     int it = 0;
     bool timed_batch = false;
     int batch = check_every;
-    double prev_rn = -1.0;
-    int prev_it = 0;
+    CheckState cs;
     bool wave_pending = false;
     for (;;) {
         const int nrec = launch_defect(L, x, h->beta, h->gamma, h->diag, h->W, h->ib, h->rho,
-                                       h->dlt, h->partials, h->stream);
+                                       h->dlt, h->partials, h->partials + 3 * kPartCap,
+                                       h->stream);
         h->launches += 1;
         CK_LAUNCH("defect");
-        if ((st = reduce_into(h, 3, nrec))) return st;   // scal[3..5] = sum r^2, min u, max u
+        // scal[3..6] = sum r^2, min u, max u, max |r|
+        if ((st = reduce_into(h, 3, nrec, true))) return st;
         if ((st = fetch_scal(h))) return st;
         if (wave_pending) {
             wave_pending = false;
@@ -347,16 +381,16 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
         out.bnorm = bn;
         out.umin = h->host_scal[4];
         out.umax = h->host_scal[5];
+        out.res_inf = h->host_scal[6];
+        out.bmax = std::max(std::fabs(h->host_scal[1]), std::fabs(h->host_scal[2]));
         if (!std::isfinite(rn))
             return fail(h, SEG4D_ERR_NOT_CONVERGED, "residual is not finite");
-        if (rn <= tol * bn) {
+        if (check_decision(cs, rn, bn, out.res_inf, out.bmax, it, tol, tol_inf, check_every,
+                           mixed, batch) != kGoOn) {
             out.converged = true;
             return SEG4D_OK;
         }
         if (it >= max_iters) return SEG4D_OK;   // not converged; caller reports it
-        batch = next_check_batch(rn, prev_rn, it, prev_it, tol, bn, check_every, mixed);
-        prev_rn = rn;
-        prev_it = it;
         const int n = std::min(batch, max_iters - it);
         CK(cudaEventRecord(h->evs0, h->stream));
         if (mixed) {
@@ -572,7 +606,7 @@ seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
     const bool mixed = h->p.precision == 1;
     SolveOut so;
     seg4d_status st = solve_system(h, h->u, brec, h->p.omega, h->p.tol, h->p.max_iters,
-                                   h->p.check_every, so, mixed);
+                                   h->p.check_every, so, mixed, h->p.tol_inf);
     if (st) return st;
     sweeps += so.iters;
     if (info) {
@@ -582,6 +616,8 @@ seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
         info->res_rel = so.bnorm > 0 ? so.res / so.bnorm : so.res;
         info->umin = so.umin;
         info->umax = so.umax;
+        info->res_inf = so.res_inf;
+        info->bmax = so.bmax;
         info->status = so.converged ? SEG4D_OK : SEG4D_ERR_NOT_CONVERGED;
     }
     if (!so.converged)
@@ -668,6 +704,7 @@ void seg4d_default_params(seg4d_params *p)
     p->omega = 1.8;
     p->omega_smooth = 1.0;
     p->tol = 1e-5;
+    p->tol_inf = 1e-5;
     p->tol_smooth = 1e-6;
     p->max_iters = 20000;
     p->check_every = 10;
@@ -729,7 +766,7 @@ seg4d_status seg4d_create_ex(const seg4d_dims *dims, void *cuda_stream, int flag
         {(void **)&h->gamma, 2 * S * 4}, {(void **)&h->diag, 2 * S * 4},
         {(void **)&h->W, 8 * S * 4},     {(void **)&h->G, 16 * S * 4},
         {(void **)&h->owner, 2 * S * 4},
-        {(void **)&h->partials, 3 * kPartCap * sizeof(double)},
+        {(void **)&h->partials, 4 * kPartCap * sizeof(double)},
         {(void **)&h->scal, 8 * sizeof(double)},
         {(void **)&h->wave_ctrl, (4 + (size_t)wave_tiles(L)) * sizeof(unsigned)},
         {(void **)&h->d_check, 4 * sizeof(unsigned)},
@@ -812,6 +849,8 @@ seg4d_status seg4d_set_params(seg4d *h, const seg4d_params *p)
         return fail(h, SEG4D_ERR_INVALID, "omega and omega_smooth must lie in (0, 2)");
     if (!finite_pos(p->tol) || !finite_pos(p->tol_smooth))
         return fail(h, SEG4D_ERR_INVALID, "tol and tol_smooth must be finite and > 0");
+    if (!std::isfinite(p->tol_inf) || p->tol_inf < 0)
+        return fail(h, SEG4D_ERR_INVALID, "tol_inf must be finite and >= 0");
     if (p->max_iters < 1 || p->check_every < 1)
         return fail(h, SEG4D_ERR_INVALID, "max_iters and check_every must be >= 1");
     if (p->precision != 0 && p->precision != 1)

@@ -139,16 +139,23 @@ __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_bsweep(
                                row, s0, rp);
 }
 
-// per-window fixed-order reduction of the chunk records (one block per window)
+// per-window fixed-order reduction of the chunk records (one block per
+// window) into out[4 w .. 4 w + 2]; with amax (the defect pass's per-chunk
+// max |r|), also its maximum into out[4 w + 3]
 __global__ void __launch_bounds__(256) k_breduce(const long long *__restrict__ cstarts,
                                                  const double *__restrict__ parts,
+                                                 const double *__restrict__ amax,
                                                  double *__restrict__ out)
 {
     const int w = blockIdx.x;
     Acc3 a{0.0, DBL_MAX, -DBL_MAX};
-    for (long long c = cstarts[w] + threadIdx.x; c < cstarts[w + 1]; c += blockDim.x)
+    float m = 0.0f;
+    for (long long c = cstarts[w] + threadIdx.x; c < cstarts[w + 1]; c += blockDim.x) {
         a = acc3_merge(a, Acc3{parts[3 * c], parts[3 * c + 1], parts[3 * c + 2]});
-    block_write3(a, out + 3 * w);
+        if (amax) m = fmaxf(m, (float)amax[c]);
+    }
+    block_write3(a, out + 4 * w);
+    if (amax) block_write_max(m, out + 4 * w + 3);
 }
 
 // step coefficients (coef_finish, Eq. new1) for every window, one voxel per
@@ -282,12 +289,13 @@ __global__ void __launch_bounds__(256) k_bmixed_prepare(const BWin *__restrict__
     }
 }
 
-// exact residual in flux form (flux_residual_vec; records) + rho = r * ib,
-// delta = 0; beta holds b itself.  A chunk of
+// exact residual in flux form (flux_residual_vec; records, and max |r| of the
+// chunk in amax) + rho = r * ib, delta = 0; beta holds b itself.  A chunk of
 // kChunkTiles 256-slot tiles is kChunkTiles / N tiles of 256 N-slot groups.
 __global__ void __launch_bounds__(256, 2) k_bdefect(const BWin *__restrict__ wins,
                                                     const long long *__restrict__ cstarts,
-                                                    int nwin, double *__restrict__ parts)
+                                                    int nwin, double *__restrict__ parts,
+                                                    double *__restrict__ amax)
 {
     constexpr int N = kVecF32;
     const long long b = blockIdx.x;
@@ -299,6 +307,7 @@ __global__ void __launch_bounds__(256, 2) k_bdefect(const BWin *__restrict__ win
     const long long nt = win_gtiles(L, N);
     const long long t0 = (b - cstarts[w]) * (kChunkTiles / N);
     Rec3f a = rec3f_init();
+    float ra = 0.0f;
     for (long long t = t0; t < t0 + kChunkTiles / N && t < nt; ++t) {
         RowPos rp{0, 0, 0, 0};
         int s0 = 0, row = 0;
@@ -326,6 +335,7 @@ __global__ void __launch_bounds__(256, 2) k_bdefect(const BWin *__restrict__ win
                 if (2 * (s0 + m) + e < L.n1) {
                     rh[m] = __fmul_rn(res[m], iv[m]);
                     rec3f_add(a, __fmul_rn(res[m], res[m]), xs[m]);
+                    ra = fmaxf(ra, fabsf(res[m]));
                 }
             }
             stv<N>(rho + q, rh);
@@ -333,6 +343,7 @@ __global__ void __launch_bounds__(256, 2) k_bdefect(const BWin *__restrict__ win
         }
     }
     block_write3(rec3f_acc(a), parts + 3 * b);
+    block_write_max(ra, amax + b);
 }
 
 // x <- x + delta on every slot of the tile (padding holds 0 in both)
@@ -709,7 +720,8 @@ seg4d_status ensure_parts(seg4d_batch *b, long long nchunks)
     cudaFree(b->d_parts);
     b->d_parts = nullptr;
     const size_t cap = (size_t)nchunks + nchunks / 4 + 1024;
-    if (cudaMalloc(&b->d_parts, 3 * sizeof(double) * cap) != cudaSuccess) {
+    // records (3 doubles per chunk), then the defect pass's max |r| per chunk
+    if (cudaMalloc(&b->d_parts, 4 * sizeof(double) * cap) != cudaSuccess) {
         cudaGetLastError();
         b->parts_cap = 0;
         return bfail(b, SEG4D_ERR_OOM, "batch: reduction records: allocation failed");
@@ -718,13 +730,15 @@ seg4d_status ensure_parts(seg4d_batch *b, long long nchunks)
     return SEG4D_OK;
 }
 
-// Records of a chunked kernel -> per-window (sum, min, max) in h_out.
-seg4d_status reduce_windows(seg4d_batch *b, size_t nw)
+// Records of a chunked kernel -> per-window (sum, min, max[, max |r|]) in
+// h_out[4 w ..]; with_max after the defect pass.
+seg4d_status reduce_windows(seg4d_batch *b, size_t nw, bool with_max = false)
 {
-    k_breduce<<<(unsigned)nw, 256, 0, b->stream>>>(b->d_chunk, b->d_parts, b->d_out);
+    k_breduce<<<(unsigned)nw, 256, 0, b->stream>>>(
+        b->d_chunk, b->d_parts, with_max ? b->d_parts + 3 * b->parts_cap : nullptr, b->d_out);
     b->launches += 1;
     BCK(cudaGetLastError());
-    BCK(cudaMemcpyAsync(b->h_out, b->d_out, 3 * sizeof(double) * nw, cudaMemcpyDeviceToHost,
+    BCK(cudaMemcpyAsync(b->h_out, b->d_out, 4 * sizeof(double) * nw, cudaMemcpyDeviceToHost,
                         b->stream));
     BCK(cudaStreamSynchronize(b->stream));
     return SEG4D_OK;
@@ -733,12 +747,12 @@ seg4d_status reduce_windows(seg4d_batch *b, size_t nw)
 struct SolveItem {
     Window *w;
     double bnorm;
+    double bmax;        // max |b|
     int iters;
     bool done;
     bool ok;
     int next_check;     // sweep count of the window's next stopping test
-    double prev_rn;     // residual norm at its previous test (-1: none yet)
-    int prev_it;
+    CheckState cs;      // its residual history (check_decision)
 };
 
 // Batched red-black SOR over every window of `items` (each window's d.x,
@@ -746,20 +760,21 @@ struct SolveItem {
 // solve_system in api.cu): a test is the exact flux-form residual, which
 // also sets up the correction system; the sweeps solve it for delta, and
 // u += delta precedes the next test.  Per window: stop when
-// ||b - A x|| <= tol ||b||.  Each window has its own check schedule
+// ||b - A x|| <= tol ||b|| and, with tol_inf > 0, max |b - A x| <= tol_inf
+// max |b| (the per-voxel part, as in the single-grid solve).  Each window
+// has its own check schedule
 // (next_check_batch on its own residual history): every round sweeps all
 // active windows up to the earliest pending check, then tests the windows
 // whose check is due (u += delta, then the defect pass, for those only).  A window's sweeps and tests therefore do not depend on
 // the other windows, and its result is the same alone or in any mix.
 seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double omega, double tol,
                          int max_iters, int check_every, long long &sweeps_total,
-                         bool mixed = false)
+                         bool mixed = false, double tol_inf = 0.0)
 {
     std::vector<SolveItem *> act, due;
     for (auto &it : items) {
         it.next_check = 0;
-        it.prev_rn = -1.0;
-        it.prev_it = 0;
+        it.cs = CheckState{};
         act.push_back(&it);
     }
     due = act;
@@ -779,10 +794,10 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
         const long long nch = b->n_chunk;
         if ((st = ensure_parts(b, nch))) return st;
         k_bdefect<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk, (int)ws.size(),
-                                                        b->d_parts);
+                                                        b->d_parts, b->d_parts + 3 * b->parts_cap);
         b->launches += 1;
         BCK(cudaGetLastError());
-        if ((st = reduce_windows(b, ws.size()))) return st;
+        if ((st = reduce_windows(b, ws.size(), true))) return st;
         if (timed) {
             float ms = 0.0f;
             if (cudaEventElapsedTime(&ms, b->e0, b->e1) == cudaSuccess) b->sweep_ms += ms;
@@ -790,27 +805,29 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
         }
         for (size_t i = 0; i < due.size(); ++i) {
             SolveItem *a = due[i];
-            const double rn = std::sqrt(b->h_out[3 * i]);
+            const double rn = std::sqrt(b->h_out[4 * i]);
+            const double rinf = b->h_out[4 * i + 3];
             a->w->last_res_rel = a->bnorm > 0 ? rn / a->bnorm : rn;
             if (!std::isfinite(rn)) {
                 a->done = true;
                 a->ok = false;
                 a->w->err = "residual is not finite";
-            } else if (rn <= tol * a->bnorm) {
-                a->done = true;
-                a->ok = true;
-                a->iters = it;
-            } else if (it >= max_iters) {
-                a->done = true;
-                a->ok = false;
-                a->iters = it;
-                a->w->err = "solve reached max_iters";
             } else {
-                const int n = next_check_batch(rn, a->prev_rn, it, a->prev_it, tol, a->bnorm,
-                                               check_every, mixed);
-                a->prev_rn = rn;
-                a->prev_it = it;
-                a->next_check = std::min(it + n, max_iters);
+                int n = check_every;
+                const int dec = check_decision(a->cs, rn, a->bnorm, rinf, a->bmax, it, tol,
+                                               tol_inf, check_every, mixed, n);
+                if (dec != kGoOn) {
+                    a->done = true;
+                    a->ok = true;
+                    a->iters = it;
+                } else if (it >= max_iters) {
+                    a->done = true;
+                    a->ok = false;
+                    a->iters = it;
+                    a->w->err = "solve reached max_iters";
+                } else {
+                    a->next_check = std::min(it + n, max_iters);
+                }
             }
         }
         std::vector<SolveItem *> next;
@@ -955,7 +972,8 @@ seg4d_status batch_setup(seg4d_batch *b, std::vector<Window *> &pend, long long 
         if ((st = reduce_windows(b, ws.size()))) return st;
         std::vector<SolveItem> items;
         for (size_t i = 0; i < ws.size(); ++i)
-            items.push_back(SolveItem{ws[i], std::sqrt(b->h_out[3 * i]), 0, false, false, 0, -1.0, 0});
+            items.push_back(SolveItem{ws[i], std::sqrt(b->h_out[4 * i]), 0.0, 0, false, false, 0,
+                                      CheckState{}});
         if ((st = batch_solve(b, items, p.omega_smooth, p.tol_smooth, p.max_iters, p.check_every,
                               sweeps)))
             return st;
@@ -1015,8 +1033,12 @@ seg4d_status batch_step(seg4d_batch *b, std::vector<Window *> &act, long long &s
     if ((st = reduce_windows(b, act.size()))) return st;
     std::vector<SolveItem> items;
     for (size_t i = 0; i < act.size(); ++i)
-        items.push_back(SolveItem{act[i], std::sqrt(b->h_out[3 * i]), 0, false, false, 0, -1.0, 0});
-    if ((st = batch_solve(b, items, p.omega, p.tol, p.max_iters, p.check_every, sweeps, mixed)))
+        items.push_back(SolveItem{act[i], std::sqrt(b->h_out[4 * i]),
+                                  std::max(std::fabs(b->h_out[4 * i + 1]),
+                                           std::fabs(b->h_out[4 * i + 2])),
+                                  0, false, false, 0, CheckState{}});
+    if ((st = batch_solve(b, items, p.omega, p.tol, p.max_iters, p.check_every, sweeps, mixed,
+                          p.tol_inf)))
         return st;
     std::vector<Window *> ok;
     for (auto &itm : items) {
@@ -1084,14 +1106,14 @@ seg4d_status seg4d_batch_create(size_t arena_bytes, int max_windows, void *cuda_
               cudaMalloc(&b->d_tile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMalloc(&b->d_ptile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMalloc(&b->d_seed, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
-              cudaMalloc(&b->d_out, 3 * sizeof(double) * max_windows) == cudaSuccess &&
+              cudaMalloc(&b->d_out, 4 * sizeof(double) * max_windows) == cudaSuccess &&
               cudaMallocHost(&b->h_wins, sizeof(BWin) * max_windows) == cudaSuccess &&
               cudaMallocHost(&b->h_chunk, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMallocHost(&b->h_tile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMallocHost(&b->h_ptile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMallocHost(&b->h_seed, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaEventCreate(&b->ev_table) == cudaSuccess &&
-              cudaMallocHost(&b->h_out, 3 * sizeof(double) * max_windows) == cudaSuccess &&
+              cudaMallocHost(&b->h_out, 4 * sizeof(double) * max_windows) == cudaSuccess &&
               cudaEventCreate(&b->e0) == cudaSuccess && cudaEventCreate(&b->e1) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -1121,7 +1143,8 @@ seg4d_status seg4d_batch_set_params(seg4d_batch *b, const seg4d_params *p)
     if ((p->precision != 0 && p->precision != 1) || !(p->omega > 0 && p->omega < 2) ||
         !(p->omega_smooth > 0 && p->omega_smooth < 2) || !(p->tol > 0) || !(p->tol_smooth > 0) ||
         p->max_iters < 1 || p->check_every < 1 || !(p->tau > 0) || !(p->eps > 0) ||
-        !(p->sigma_t > 0) || !(p->r_ball > 0) || !(p->R_init > 0) || !(p->v_init > 0))
+        !(p->sigma_t > 0) || !(p->r_ball > 0) || !(p->R_init > 0) || !(p->v_init > 0) ||
+        !(p->tol_inf >= 0) || !std::isfinite(p->tol_inf))
         return bfail(b, SEG4D_ERR_INVALID, "batch_set_params: invalid parameters");
     for (int d = 0; d < 4; ++d)
         if (!(p->h[d] > 0) || !std::isfinite(p->h[d]))
@@ -1161,6 +1184,20 @@ seg4d_status seg4d_batch_add(seg4d_batch *b, const seg4d_dims *dims, const float
         b->arena.release(w.off_main, w.bytes_main);
         return bfail(b, SEG4D_ERR_OOM, "batch_add: no room in the arena (admission refused)");
     }
+    // both blocks go back to the arena on every error path below, until the
+    // window is in the table
+    struct BlockGuard {
+        Arena &a;
+        size_t o1, n1, o2, n2;
+        bool armed = true;
+        ~BlockGuard()
+        {
+            if (armed) {
+                a.release(o1, n1);
+                a.release(o2, n2);
+            }
+        }
+    } guard{b->arena, w.off_main, w.bytes_main, w.off_img, w.bytes_img};
     w.has_img = true;
     carve(b, w);
     // zero the main block (padding slots must read as zero)
@@ -1180,6 +1217,7 @@ seg4d_status seg4d_batch_add(seg4d_batch *b, const seg4d_dims *dims, const float
     b->next_id += 1;
     *id_out = w.id;
     b->wins[w.id] = w;
+    guard.armed = false;
     return SEG4D_OK;
 }
 

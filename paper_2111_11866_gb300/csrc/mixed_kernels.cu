@@ -67,8 +67,9 @@ __global__ void __launch_bounds__(256) k_mixed_prepare(Layout L, const float *__
 
 // Defect pass: the exact residual r of every voxel in flux form
 // (flux_residual_vec); rho = r / D_b, delta = 0; records (sum r^2, min u,
-// max u).  b is the prepared beta array.  Work items and grid as the
-// residual kernel: item t = 2 * tile + colour over the sweep's tiles.
+// max u) in `partials` and max |r| of each block in amax[block].  b is the
+// prepared beta array.  Work items and grid as the residual kernel: item
+// t = 2 * tile + colour over the sweep's tiles.
 template <int N>
 __global__ void __launch_bounds__(256, SEG4D_DEFECT_MINB) k_defect(Layout L, const float *__restrict__ u,
                                                    const float *__restrict__ b,
@@ -79,9 +80,11 @@ __global__ void __launch_bounds__(256, SEG4D_DEFECT_MINB) k_defect(Layout L, con
                                                    float *__restrict__ rho,
                                                    float *__restrict__ delta,
                                                    double *__restrict__ partials,
+                                                   double *__restrict__ amax,
                                                    ItemDecode dec, unsigned items)
 {
     Rec3f a = rec3f_init();
+    float ra = 0.0f;   // max |r| of the thread's voxels
     for (unsigned t = blockIdx.x; t < items; t += gridDim.x) {
         int C, chunk;
         RowPos rp;
@@ -111,12 +114,14 @@ __global__ void __launch_bounds__(256, SEG4D_DEFECT_MINB) k_defect(Layout L, con
             if (2 * (s0 + m) + e < L.n1) {
                 rh[m] = __fmul_rn(res[m], iv[m]);
                 rec3f_add(a, __fmul_rn(res[m], res[m]), xs[m]);
+                ra = fmaxf(ra, fabsf(res[m]));
             }
         }
         stv<N>(rho + q, rh);
         stv<N>(delta + q, zero);
     }
     block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
+    block_write_max(ra, amax + blockIdx.x);
 }
 
 // Before an FP32 solve (the correction sweeps run on the scaled system, see
@@ -188,13 +193,13 @@ void launch_mixed_prepare(const Layout &L, const float *W, const float *gamma, c
 
 int launch_defect(const Layout &L, const float *u, const float *b, const float *gamma,
                   const float *diag, const float *W, const float *ib, float *rho, float *delta,
-                  double *partials, cudaStream_t st)
+                  double *partials, double *amax, cudaStream_t st)
 {
     const int nch = (L.P + 32 * kDefectN - 1) / (32 * kDefectN);
     const long long items = item_count(L, nch);
     const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
     k_defect<kDefectN><<<blocks, 256, 0, st>>>(L, u, b, gamma, diag, W, ib, rho, delta, partials,
-                                               make_item_decode(L, nch), (unsigned)items);
+                                               amax, make_item_decode(L, nch), (unsigned)items);
     return blocks;
 }
 

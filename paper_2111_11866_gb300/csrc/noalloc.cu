@@ -32,9 +32,11 @@ constexpr int kMaxDevices = 64;
 // that loads the library, held until the process exits.
 static __device__ __align__(256) double g_noalloc_records[2 * kMaxBlocks];
 
+// Device address of the scratch array per device, cached once a lookup has
+// succeeded; a failed lookup (for example one made during a stream capture)
+// is not cached, so the next call tries again.
 double *g_records_addr[kMaxDevices] = {};
-std::once_flag g_records_once[kMaxDevices];
-cudaError_t g_records_err[kMaxDevices] = {};
+std::mutex g_records_mutex[kMaxDevices];
 
 
 // r_v = b_v - diag_v u_v + sum_f off[v][f] u_nb(f) over the faces whose
@@ -148,21 +150,32 @@ extern "C" seg4d_status seg4d_residual_norms_noalloc(const seg4d_dims *dims, con
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return noalloc_fail(SEG4D_ERR_CUDA, std::string("residual_norms_noalloc: no current "
                                                         "device: ") + cudaGetErrorString(e));
-    // once per device, with that device current: the device address of the
-    // scratch array (its host-side name is only a stand-in)
-    std::call_once(g_records_once[dev], [dev]() {
-        void *p = nullptr;
-        g_records_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_records);
-        if (g_records_err[dev] == cudaSuccess) g_records_addr[dev] = (double *)p;
-    });
-    if (g_records_err[dev] != cudaSuccess || !g_records_addr[dev])
-        return noalloc_fail(SEG4D_ERR_CUDA, std::string("residual_norms_noalloc: scratch address: ") +
-                                                cudaGetErrorString(g_records_err[dev]));
+    // with that device current: the device address of the scratch array (its
+    // host-side name is only a stand-in), looked up until a lookup succeeds
+    double *records = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_records_mutex[dev]);
+        if (!g_records_addr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_records);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();   // the failed lookup's error is reported here, not later
+                return noalloc_fail(SEG4D_ERR_CUDA,
+                                    std::string("residual_norms_noalloc: scratch address: ") +
+                                        cudaGetErrorString(e));
+            }
+            g_records_addr[dev] = (double *)p;
+        }
+        records = g_records_addr[dev];
+    }
     const int nblocks = (int)((rows + kRowsPerBlock - 1) / kRowsPerBlock);
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    // an error left pending by earlier, unrelated work must not be reported
+    // as this call's launch failure
+    cudaGetLastError();
     k_residual_records<<<nblocks, kThreads, 0, st>>>(dims->n1, dims->n2, dims->n3, dims->n4, u, b,
-                                                     diag, off, g_records_addr[dev]);
-    k_records_final<<<1, 1024, 0, st>>>(g_records_addr[dev], nblocks, result);
+                                                     diag, off, records);
+    k_records_final<<<1, 1024, 0, st>>>(records, nblocks, result);
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return noalloc_fail(SEG4D_ERR_CUDA, std::string("residual_norms_noalloc: launch: ") +

@@ -163,9 +163,10 @@ void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta
 void launch_mixed_prepare(const Layout &L, const float *W, const float *gamma, const float *diag,
                           void *Wb, float *gb, float *ib, cudaStream_t st);
 // returns the number of per-block records written to `partials`
+// amax: per-block max |r| (one double per record)
 int launch_defect(const Layout &L, const float *u, const float *b, const float *gamma,
                   const float *diag, const float *W, const float *ib, float *rho, float *delta,
-                  double *partials, cudaStream_t st);
+                  double *partials, double *amax, cudaStream_t st);
 // red-black SOR on the BF16 correction system A_b delta = r (solve_kernels.cu)
 void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *rho,
                         const float *gb, const void *Wb, float omega, cudaStream_t st);
@@ -180,7 +181,9 @@ void launch_plain_prepare(const Layout &L, const float *gamma, const float *diag
                           float *ib, cudaStream_t st);
 void launch_apply_scaled(const Layout &L, float *u, const float *delta, const float *rs,
                          cudaStream_t st);
-void launch_reduce_partials(const double *partials, int nparts, double *out, cudaStream_t st);
+// out[0..2] = (sum, min, max) of the records; with amax, out[3] = max of amax
+void launch_reduce_partials(const double *partials, int nparts, double *out, cudaStream_t st,
+                            const double *amax = nullptr);
 
 // Sweeps until the next stopping test of a solve.  After two checks with
 // r_now < r_prev, rho = (r_now/r_prev)^(1/sweeps) and need = log(tol*||b|| /
@@ -196,11 +199,31 @@ void launch_reduce_partials(const double *partials, int nparts, double *out, cud
 int next_check_batch(double rn, double prev_rn, int it, int prev_it, double tol, double bnorm,
                      int check_every, bool mixed);
 
+// Stopping decision at a check of a solve.  The test has two parts:
+// ||r||_2 <= tol ||b||_2 and, with tol_inf > 0, max |r| <= tol_inf max |b|
+// (a per-voxel bound, ||A^-1||_inf <= 1).  When the 2-norm part holds but the
+// per-voxel part does not, and max |r| has stopped falling -- less than 1 %
+// per sweep over at least check_every sweeps since the previous check --
+// the iterate has reached the floor that FP32 rounding of u sets for max |r|
+// (about D ulp(u) at a voxel), and the solve stops there (kStopFloor; the
+// achieved max |r| is what the caller reports).  Otherwise `batch` is the
+// number of sweeps to the next check: from the 2-norm history, or, once the
+// 2-norm part holds, from the max |r| history (at least check_every).  Only
+// the solve's own residual history enters.
+struct CheckState {
+    double prev_rn = -1.0, prev_inf = -1.0;
+    int prev_it = 0;
+};
+enum { kGoOn = 0, kStop = 1, kStopFloor = 2 };
+int check_decision(CheckState &cs, double rn, double bn, double rinf, double bmax, int it,
+                   double tol, double tol_inf, int check_every, bool mixed, int &batch);
+
 // message of the last failed handle-free call of this thread (api.cu)
 std::string &handle_free_error();
 
 // number of per-block partial records (3 doubles each: sum, min, max) the
-// reduction kernels use; the scratch array holds 3 * kPartBlocks doubles.
+// reduction kernels use; the scratch array holds 4 * kPartCap doubles: the
+// records, then one max |r| per record of the defect pass.
 constexpr int kPartBlocks = 1024;
 constexpr int kPartThreads = 256;
 // blocks (records) of the item loops of the coefficient, defect and scaling

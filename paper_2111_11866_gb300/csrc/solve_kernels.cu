@@ -295,7 +295,10 @@ int wave_max_ctas_per_sm()
     return nb < 1 ? 1 : nb;
 }
 
-// Launches of at most 2^31 items each; ctrl is zeroed before each.
+// Launches of at most 2^31 items each.  The caller zeroes ctrl before the
+// first; between launches only the ticket, the abort flag and done[] are
+// cleared, so an error raised by an earlier launch (ctrl[2]) survives to the
+// host's check after the last one.
 void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta,
                        const float *gamma, const float *W, float omega, unsigned *ctrl, int ctas,
                        int test_wait, cudaStream_t st)
@@ -306,8 +309,10 @@ void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta
     for (int done_sw = 0; done_sw < nsweeps;) {
         const int n = std::min(nsweeps - done_sw, max_sweeps);
         const WaveGeo G = wave_geo(L, n);
-        if (done_sw > 0)
-            cudaMemsetAsync(ctrl, 0, (4 + (size_t)G.Tf) * sizeof(unsigned), st);
+        if (done_sw > 0) {
+            cudaMemsetAsync(ctrl, 0, 2 * sizeof(unsigned), st);
+            cudaMemsetAsync(ctrl + 4, 0, (size_t)G.Tf * sizeof(unsigned), st);
+        }
         if (gamma)
             k_sweep_wave<false><<<ctas, 32 * kWaveWarps, 0, st>>>(L, G, x, beta, gamma, W, omega, n,
                                                                  ctrl, test_wait);
@@ -369,20 +374,27 @@ void launch_scaled_weights(const Layout &L, const float *W, float *Ws, const flo
                                              (unsigned)red_items);
 }
 
-// Deterministic final reduction of the per-block records (one block).
+// Deterministic final reduction of the per-block records (one block); with
+// amax, also the maximum of amax[0..n) into out[3].
 __global__ void __launch_bounds__(1024) k_reduce(const double *__restrict__ partials, int n,
+                                                 const double *__restrict__ amax,
                                                  double *__restrict__ out)
 {
     Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    float m = 0.0f;
 #pragma unroll 4
-    for (int b = threadIdx.x; b < n; b += blockDim.x)
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
         a = acc3_merge(a, Acc3{partials[3 * b], partials[3 * b + 1], partials[3 * b + 2]});
+        if (amax) m = fmaxf(m, (float)amax[b]);   // amax holds FP32 values
+    }
     block_write3(a, out);
+    if (amax) block_write_max(m, out + 3);
 }
 
-void launch_reduce_partials(const double *partials, int nparts, double *out, cudaStream_t st)
+void launch_reduce_partials(const double *partials, int nparts, double *out, cudaStream_t st,
+                            const double *amax)
 {
-    k_reduce<<<1, 1024, 0, st>>>(partials, nparts, out);
+    k_reduce<<<1, 1024, 0, st>>>(partials, nparts, amax, out);
 }
 
 // Coefficients of the step system (coef_finish, Eq. new1) from

@@ -58,6 +58,26 @@ __device__ inline void block_write3(Acc3 a, double *rec)
     }
 }
 
+// Block-wide maximum of a non-negative float; thread 0 writes it as a double.
+// Must follow the block's other reductions (it reuses no shared memory of
+// theirs, but every thread of the block must call it).
+__device__ inline void block_write_max(float v, double *out)
+{
+    __shared__ float shm[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (lane == 0) shm[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        float b = lane < nw ? shm[lane] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b = fmaxf(b, __shfl_down_sync(0xffffffffu, b, o));
+        if (lane == 0) *out = (double)b;
+    }
+}
+
 struct RowPos {
     int j, k, l, p;
 };

@@ -47,3 +47,20 @@ def label_mismatch_outside_band(u_gpu, u_ref, iso=0.5):
         b[1:] |= cross
         b[:-1] |= cross
     return int((diff & ~band).sum())
+
+
+def _oracle_job(args):
+    image, seeds, nsteps, P, omp = args
+    u, info = O.segment(image.astype(np.float64), seeds, P, nsteps=nsteps, omp=omp)
+    return u, info
+
+
+def oracle_segment_many(jobs, P, procs=None):
+    """O.segment of every (image, seeds, nsteps) job on the plain oracle build,
+    in a pool of spawned processes (one job per process at a time)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    procs = procs or max(1, min(len(jobs), os.cpu_count() or 1))
+    with cf.ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_oracle_job, [(img, s, n, P, False) for img, s, n in jobs]))

@@ -1,0 +1,87 @@
+"""End-to-end parity on the whole medium workload (128x128x64 x 32 frames,
+33.5M voxels): the CUDA path after several whole time steps against the FP64
+oracle solved to 1e-12, voxel by voxel, in FP32 and in mixed precision.
+
+The oracle runs on its OpenMP build (red-black SOR with the frames split among
+the host's threads, the paper's OpenMP scheme); solved to 1e-12 it reaches
+the same solutions as the plain build.  A few steps take one to two minutes
+on a 16-core host.
+
+Bars: |u_gpu - u_oracle| <= 1e-4 max|u_oracle| per voxel, and identical labels
+(u >= 0.5) outside a one-voxel band of the oracle's level set.  The stopping
+test's per-voxel part (max |r| against max |b|) is also checked on the
+returned iterate.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2111_11866_gb300 import _lib, synth
+
+from gpu_common import REL_TOL, gpu_run, label_mismatch_outside_band, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+NSTEPS = 3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2111_11866_gb300 import build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def medium():
+    try:
+        O.lib(omp=True)
+    except OSError as e:   # no OpenMP runtime on this host
+        pytest.skip(f"oracle OpenMP build unavailable: {e}")
+    c = synth.medium()
+    p = _lib.Params.defaults()
+    ref_u, ref_info = O.segment(c.image.astype(np.float64), c.seeds, oracle_params(p),
+                                nsteps=NSTEPS, omp=True)
+    assert ref_info["status"] == O.OR_OK, ref_info
+    return c, ref_u
+
+
+def _check(u, r):
+    err = float(np.abs(u - r).max())
+    scale = float(np.abs(r).max())
+    assert err <= REL_TOL * scale, (err, scale)
+    assert label_mismatch_outside_band(u, r) == 0
+    assert (r >= 0.5).sum() > 10000   # the segmentation is not trivial
+    return err / scale
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_medium_end_to_end(medium, precision):
+    """Default parameters: every solve stops on both parts of the stopping
+    test, so the last one ends with max |r| <= tol_inf max |b| (each voxel
+    within that of the exact solve, since ||A^-1||_inf <= 1)."""
+    c, r = medium
+    p = _lib.Params.defaults()
+    p.precision = precision
+    assert p.tol_inf > 0
+    gpu = gpu_run(c.image, c.seeds, NSTEPS, p)
+    info = gpu["info"]
+    assert info["steps_done"] == NSTEPS and info["status"] == _lib.OK, info
+    assert info["res_inf"] <= p.tol_inf * info["bmax"], info
+    rel = _check(gpu["u"], r)
+    print(f"precision {precision}: max|du|/max|u| = {rel:.3e}, last solve "
+          f"res_rel = {info['res_rel']:.3e}, max|r|/max|b| = {info['res_inf'] / info['bmax']:.3e}")
+
+
+def test_medium_two_norm_rule_alone(medium):
+    """With the per-voxel part off (tol_inf = 0) the 2-norm rule alone still
+    meets the parity bar on this workload."""
+    c, r = medium
+    p = _lib.Params.defaults()
+    p.tol_inf = 0.0
+    gpu = gpu_run(c.image, c.seeds, NSTEPS, p)
+    assert gpu["info"]["status"] == _lib.OK
+    rel = _check(gpu["u"], r)
+    print(f"2-norm rule alone: max|du|/max|u| = {rel:.3e}")

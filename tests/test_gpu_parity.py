@@ -84,6 +84,21 @@ def test_face_coefficients(small):
     assert (gpu["f_G"] > 0).all() and (gpu["f_G"] <= 1).all()
 
 
+def test_face_coefficients_on_identical_images(small):
+    """G from the GPU's own presmoothed images, oracle against GPU: the only
+    difference left is FP32 arithmetic.  The diamond differences of FP32
+    images carry about 1e-5 of absolute error in |grad I| (h = 0.01), and
+    |dG/ds| s / G <= 2 sqrt(K) s/(1 + K s^2) <= 1, so 2e-5 relative bounds it;
+    a coefficient wrong by 100 % at the edges, where G is about 1e-3, fails."""
+    gpu, _, p = small
+    P = oracle_params(p)
+    G = O.face_G(gpu["f_Isig0"].astype(np.float64), gpu["f_IsigTH"].astype(np.float64), P.h,
+                 P.K, P.delta, P.vartheta)
+    rel = np.abs(gpu["f_G"] - G) / G
+    assert rel.max() <= 2e-5, rel.max()
+    assert G.min() < 0.05   # the case has real edges
+
+
 def test_initial_condition(small):
     gpu, ref, _ = small
     np.testing.assert_allclose(gpu["f_u"], ref["u0"], atol=1e-6)
@@ -141,12 +156,18 @@ def test_solve_alone_from_given_u():
         ug = s.read_u()
         off_g = s.read_field("off")
         diag_g = s.read_field("diag")
+        G_g = s.read_field("G")
     img = c.image.astype(np.float64)
     ITH = O.threshold(img, c.seeds, P.r_ball, P.lambda_th)
     G = O.face_G(O.presmooth(img, P.h, P.sigma_t)[0], O.presmooth(ITH, P.h, P.sigma_t)[0], P.h,
                  P.K, P.delta, P.vartheta)
     diag, off = O.assemble(u0.astype(np.float64), G, P.h, P.tau, P.eps)
     ur, _ = O.solve(diag, off, u0.astype(np.float64), omega=1.8, tol=1e-12)
+    # identical inputs (the GPU's own G and the same u): FP32 arithmetic only
+    diag_i, off_i = O.assemble(u0.astype(np.float64), G_g.astype(np.float64), P.h, P.tau, P.eps)
+    np.testing.assert_allclose(diag_g, diag_i, rtol=1e-5)
+    inner = off_g != 0
+    np.testing.assert_allclose(off_g[inner], off_i[inner], rtol=1e-5)
     np.testing.assert_allclose(diag_g, diag, rtol=2e-3)
     # interior faces only (the ABI reports faces to the boundary as 0)
     interior = off_g != 0

@@ -40,13 +40,15 @@ def test_struct_layouts_match_header(tmp_path):
                    "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(seg4d_params),"
                    " sizeof(seg4d_seed), sizeof(seg4d_info), sizeof(seg4d_dims),"
                    " offsetof(seg4d_info, sweeps_total), offsetof(seg4d_params, max_iters));"
+                   "printf(\"%zu %zu\\n\", offsetof(seg4d_params, tol_inf), offsetof(seg4d_info, res_inf));"
                    "return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     got = [int(x) for x in out]
     want = [C.sizeof(_lib.CParams), C.sizeof(_lib.CSeed), C.sizeof(_lib.CInfo),
-            C.sizeof(_lib.CDims), _lib.CInfo.sweeps_total.offset, _lib.CParams.max_iters.offset]
+            C.sizeof(_lib.CDims), _lib.CInfo.sweeps_total.offset, _lib.CParams.max_iters.offset,
+            _lib.CParams.tol_inf.offset, _lib.CInfo.res_inf.offset]
     assert got == want
 
 

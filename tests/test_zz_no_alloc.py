@@ -1,13 +1,15 @@
 """seg4d_residual_norms_noalloc, the entry point for callers that cannot
 allocate device memory (their memory belongs to their own pool or budget, or
 they cannot take the synchronisation cudaMalloc/cudaFree may imply): it must
-give the same residual norms as the allocating solve path, call after call.
+give the same residual norms as the allocating solve path and as the FP64
+oracle's residual of the same arrays, call after call.
 
 This file is collected last on purpose, so that a run stopping at the first
 failure has already run every other test."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2111_11866_gb300 import _lib, synth
 
 pytestmark = pytest.mark.gpu
@@ -66,6 +68,12 @@ def test_noalloc_matches_allocating_path_twice():
         rn, bn = result.tolist()
         assert abs(rn - info["res_l2"]) <= REL_TOL * info["res_l2"], (dims, rn, info["res_l2"])
         assert abs(bn - info["bnorm"]) <= REL_TOL * info["bnorm"], (dims, bn, info["bnorm"])
+        # and the FP64 oracle's residual of the very same arrays
+        r = O.residual(diag.cpu().numpy(), off.cpu().numpy(), b.cpu().numpy(), u.cpu().numpy())
+        ro = float(np.sqrt((r * r).sum()))
+        bo = float(np.sqrt((b.cpu().double() ** 2).sum()))
+        assert abs(rn - ro) <= REL_TOL * ro, (dims, rn, ro)
+        assert abs(bn - bo) <= REL_TOL * bo, (dims, bn, bo)
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
