@@ -191,7 +191,7 @@ def _crop_seeds(seeds, org, n=CROP):
     return sh[keep]
 
 
-def large_crop(img=None, frames=48, n=CROP):
+def large_crop(img=None, frames=48, depth=128, n=CROP):
     """The CPU baselines' sample of the large workload: an n-sized crop (first
     n4 frames) around the nucleus nearest the grid centre.  From the device
     image when given, else the first n4 frames generated on the host by the
@@ -199,7 +199,8 @@ def large_crop(img=None, frames=48, n=CROP):
     description)."""
     import numpy as np
     from paper_2111_11866_gb300 import synth
-    dims = (512, 512, 128, frames)
+    dims = (512, 512, depth, frames)
+    n = tuple(min(a, b) for a, b in zip(n, dims))
     seeds, count, gen = synth.nuclei_frames(3, dims, 1.0 / 40 ** 3, "cpu" if img is None else
                                             img.device)
     x0, y0, z0 = _crop_box(seeds, dims, n)
@@ -212,7 +213,8 @@ def large_crop(img=None, frames=48, n=CROP):
             crop[l] = f[z0:z0 + n3, y0:y0 + n2, x0:x0 + n1].numpy()
             if l + 1 == n4:
                 break
-    desc = f"{n1}x{n2}x{n3}x{n4} crop at ({x0},{y0},{z0},0) of the large 512x512x128x{frames} grid"
+    desc = (f"{n1}x{n2}x{n3}x{n4} crop at ({x0},{y0},{z0},0) of the large "
+            f"512x512x{depth}x{frames} grid")
     return crop, _crop_seeds(seeds, (x0, y0, z0), n), desc
 
 
@@ -287,10 +289,10 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def _config_large(frames=48, nsteps=20):
-    return {"workload": f"large full grid 512x512x128x{frames}, 1 nucleus per 40^3 voxels, "
-                        f"{nsteps} steps", "n1": 512, "n2": 512, "n3": 128, "n4": frames,
-            "voxels": 512 * 512 * 128 * frames, "time_steps": nsteps,
+def _config_large(frames=48, nsteps=20, depth=128):
+    return {"workload": f"large full grid 512x512x{depth}x{frames}, 1 nucleus per 40^3 voxels, "
+                        f"{nsteps} steps", "n1": 512, "n2": 512, "n3": depth, "n4": frames,
+            "voxels": 512 * 512 * depth * frames, "time_steps": nsteps,
             "parallelism": "replicas",
             "l2": "inputs larger than L2 (about 200 GB resident)"}
 
@@ -350,12 +352,13 @@ def run_headline(args, params, local, dist, world):
     import torch
     from paper_2111_11866_gb300 import _lib, synth
 
-    img_d, seeds, nsteps, meta = synth.large("cuda", frames=args.large_frames)
+    img_d, seeds, nsteps, meta = synth.large("cuda", frames=args.large_frames,
+                                             depth=args.large_depth)
     if args.time_steps is not None:
         nsteps = args.time_steps
     dims = tuple(reversed(img_d.shape))
     nvox = img_d.numel()
-    crop = large_crop(img_d, frames=args.large_frames)   # CPU baselines' sample
+    crop = large_crop(img_d, frames=args.large_frames, depth=args.large_depth)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     seg = _lib.Seg4D(dims, stream=stream, params=params)
@@ -418,7 +421,8 @@ def run_headline(args, params, local, dist, world):
         last = infos[-1]
         res = {"value": value, "elapsed_ms": elapsed_ms, "nvox": nvox, "sweeps": sweeps,
                "launches": launches, "clocks": clocks, "e2e": e2e, "crop": crop,
-               "config": _config_large(args.large_frames, nsteps), "meta": meta,
+               "config": _config_large(args.large_frames, nsteps, args.large_depth),
+               "meta": meta,
                "sweep_rate": nvox * sweeps / (sweep_ms / 1000.0) if sweep_ms > 0 else None,
                "roofline": _roofline(nvox, sweeps, sweep_ms, sweep_launches, ALG_BYTES_SCALED,
                                      SWEEP_KERNELS[params.sweep_variant],
@@ -665,6 +669,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--large-frames", type=int, default=48,
                     help="frames of the large grid (fewer: the same planes, for profiling)")
+    ap.add_argument("--large-depth", type=int, default=128,
+                    help="z-planes of the large grid (fewer: the same rows, for profiling)")
     ap.add_argument("--time-steps", type=int, default=None,
                     help="override the large workload's 20 time steps (profiling runs only)")
     ap.add_argument("--medium-steps", type=int, default=3,

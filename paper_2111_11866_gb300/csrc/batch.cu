@@ -31,6 +31,10 @@
 namespace seg4d_impl {
 
 constexpr int kChunkTiles = 16;   // tiles per block of the reduction kernels
+#ifndef SEG4D_CHECK_GRID
+#define SEG4D_CHECK_GRID 4
+#endif
+constexpr int kCheckGrid = SEG4D_CHECK_GRID;   // batch checks fall on multiples of this
 
 struct BWin {
     Layout L;
@@ -826,7 +830,13 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
                     a->iters = it;
                     a->w->err = "solve reached max_iters";
                 } else {
-                    a->next_check = std::min(it + n, max_iters);
+                    // checks land on multiples of kCheckGrid sweeps, so that the
+                    // windows' own schedules meet in fewer rounds (each round
+                    // costs a defect pass, a reduction and a host wait); the grid
+                    // is fixed, so a window's schedule still depends on nothing
+                    // but its own residuals
+                    const int nc = (it + n + kCheckGrid - 1) / kCheckGrid * kCheckGrid;
+                    a->next_check = std::min(nc, max_iters);
                 }
             }
         }

@@ -221,12 +221,13 @@ def nuclei_device(seed: int, n, density_per_voxel: float, device, nsteps: int = 
     return img, seeds, nsteps, {"count": count, "name": name}
 
 
-def large(device, seed: int = 3, frames: int = 48):
+def large(device, seed: int = 3, frames: int = 48, depth: int = 128):
     """512x512x128 space x 48 frames (1.61G voxels), one nucleus per 40^3
     voxels (about 524), 20 steps; built on the device (nuclei_device).  Fewer
-    frames give the same planes at a size a profiler can replay."""
-    return nuclei_device(seed, (512, 512, 128, frames), 1.0 / 40 ** 3, device, nsteps=20,
-                         name=f"large 512x512x128x{frames}, 1 nucleus per 40^3")
+    frames (or z-planes) give the same 512x512 rows at a size a profiler can
+    replay."""
+    return nuclei_device(seed, (512, 512, depth, frames), 1.0 / 40 ** 3, device, nsteps=20,
+                         name=f"large 512x512x{depth}x{frames}, 1 nucleus per 40^3")
 
 
 def paper_scale(device, seed: int = 7):
