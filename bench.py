@@ -44,8 +44,7 @@ sys.path.insert(0, ROOT)
 ALG_BYTES_SCALED = 28.0
 ALG_BYTES_UNSCALED = 32.0
 FALLBACK_HBM_GBS = 6800.0
-SWEEP_KERNELS = {0: "k_sweep_wave (fused frame pipeline, several sweeps per launch)",
-                 1: "k_sweep_vec (one colour of a red-black sweep per launch, 2 voxels/thread)"}
+SWEEP_KERNEL = "k_sweep_vec (one colour of a red-black sweep per launch, 2 voxels/thread)"
 # DRAM traffic of the sweep comes from a committed ncu summary: its
 # "bench-record:" line gives the bytes per voxel update and the hash of the
 # kernel sources at capture time; a record whose hash differs from the
@@ -425,7 +424,7 @@ def run_headline(args, params, local, dist, world):
                "meta": meta,
                "sweep_rate": nvox * sweeps / (sweep_ms / 1000.0) if sweep_ms > 0 else None,
                "roofline": _roofline(nvox, sweeps, sweep_ms, sweep_launches, ALG_BYTES_SCALED,
-                                     SWEEP_KERNELS[params.sweep_variant],
+                                     SWEEP_KERNEL,
                                      sweep_traffic_record("k_sweep_vec_large_planes.md")),
                "sweeps_per_segmentation": sweeps / args.steps,
                "ms_per_time_step": elapsed_ms / args.steps / nsteps,
@@ -478,7 +477,7 @@ def run_medium(args, params, local):
                     "sweeps_per_segmentation": sw / args.medium_steps,
                     "sweep_rate": nvox * sw / (sms / 1000.0),
                     "roofline": _roofline(nvox, sw, sms, sl, ALG_BYTES_SCALED,
-                                          SWEEP_KERNELS[params.sweep_variant],
+                                          SWEEP_KERNEL,
                                           sweep_traffic_record("k_sweep_vec_medium.md"))})
         u_plain = seg.read_u()
         if args.mixed_steps > 0:
@@ -686,8 +685,6 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="arrival horizon of the serving measurement (0 = skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
-    ap.add_argument("--sweep-variant", type=int, default=1, choices=[0, 1],
-                    help="0 = fused frame-pipeline sweep, 1 = one launch per colour")
     args = ap.parse_args()
 
     rank = _env_int("RANK", 0)
@@ -711,7 +708,6 @@ def main():
     from paper_2111_11866_gb300 import _lib
 
     params = _lib.Params.defaults()
-    params.sweep_variant = args.sweep_variant
     head = run_headline(args, params, local, dist, world)
 
     cpu = cpu_omp = None

@@ -46,7 +46,8 @@ typedef enum {
     SEG4D_ERR_NOT_CONVERGED = -4, /* a solve reached max_iters; u holds the last
                                      iterate and the info struct is filled          */
     SEG4D_ERR_CUDA = -5,          /* a CUDA call failed                             */
-    SEG4D_ERR_TIMEOUT = -6        /* a bounded device wait ran out                  */
+    SEG4D_ERR_TIMEOUT = -6        /* a bounded device wait ran out (no kernel of
+                                     this version waits on another)              */
 } seg4d_status;
 
 /* interior grid sizes; n4 = number of frames */
@@ -87,17 +88,10 @@ typedef struct {
                            pass r = b - A u; the sweeps solve A_b delta = r and
                            u += delta, so the fixed point is the FP32 system's.
                            Presmoothing solves are always FP32.                    */
-    int sweep_variant;  /* 0 = fused frame pipeline: one persistent launch per
-                           batch of sweeps, red of frame s and black of frame
-                           s-2 together, face weights re-read from L2;
-                           1 = one launch per colour (default, faster on the
-                           measured grids); both give identical bits         */
-    int ctas_per_sm;    /* resident CTAs per SM of the fused sweep (0 = as many
-                           as fit, at most 4)                                    */
-    int wait_test;      /* test hook, 0 normally.  1: the first work item of the
-                           fused sweep also waits for a flag that nothing sets,
-                           so its bounded wait expires (about 2 s) and the call
-                           returns SEG4D_ERR_TIMEOUT with u not valid            */
+    int sweep_variant;  /* 1: one launch per colour of each red-black sweep (the
+                           only sweep kept; other values are rejected)           */
+    int ctas_per_sm;    /* reserved, must be 0                                   */
+    int wait_test;      /* reserved, must be 0                                   */
     double tol_inf;     /* per-voxel part of the stopping test of the step solves:
                            with tol_inf > 0 a solve also needs
                            max |b - A u| <= tol_inf max |b|.  The step matrix is

@@ -17,45 +17,6 @@
 using namespace seg4d_impl;
 
 namespace seg4d_impl {
-int next_check_batch(double rn, double prev_rn, int it, int prev_it, double tol, double bnorm,
-                     int check_every, bool mixed)
-{
-    if (!(prev_rn > 0.0 && rn < prev_rn && it > prev_it && rn > 0.0)) return check_every;
-    const double gain = mixed ? 1e-2 : 1e-3;
-    const double rho = std::pow(rn / prev_rn, 1.0 / (it - prev_it));
-    const double need = std::log(tol * bnorm / rn) / std::log(rho);
-    const double cap = std::log(gain) / std::log(rho);
-    const int lo = std::max(1, check_every / 4), hi = 8 * check_every;
-    const double want = std::ceil(std::min(0.8 * need, cap));
-    return std::isfinite(want) ? (int)std::min<double>(hi, std::max<double>(lo, want))
-                               : check_every;
-}
-
-int check_decision(CheckState &cs, double rn, double bn, double rinf, double bmax, int it,
-                   double tol, double tol_inf, int check_every, bool mixed, int &batch)
-{
-    const bool l2 = rn <= tol * bn;
-    const bool inf = tol_inf <= 0.0 || rinf <= tol_inf * bmax;
-    int res = kGoOn;
-    if (l2 && inf) {
-        res = kStop;
-    } else if (l2 && cs.prev_inf > 0.0 && it - cs.prev_it >= check_every) {
-        const double rho = std::pow(rinf / cs.prev_inf, 1.0 / (it - cs.prev_it));
-        if (!(rho < 0.99)) res = kStopFloor;
-    }
-    if (res == kGoOn) {
-        if (l2)
-            batch = std::max(check_every, next_check_batch(rinf, cs.prev_inf, it, cs.prev_it,
-                                                           tol_inf, bmax, check_every, mixed));
-        else
-            batch = next_check_batch(rn, cs.prev_rn, it, cs.prev_it, tol, bn, check_every, mixed);
-    }
-    cs.prev_rn = rn;
-    cs.prev_inf = rinf;
-    cs.prev_it = it;
-    return res;
-}
-
 // message of the last failed handle-free call of this thread (seg4d_create,
 // seg4d_residual_norms_noalloc), reported by seg4d_last_error(NULL)
 std::string &handle_free_error()
@@ -83,9 +44,7 @@ struct seg4d {
     double *partials = nullptr;    // 3 * kPartCap doubles (scratch)
     double *scal = nullptr;        // 8 doubles: reduced records
     double *host_scal = nullptr;   // pinned mirror of scal
-    unsigned *wave_ctrl = nullptr; // fused-sweep control block: 4 + tiles u32
-    unsigned *host_wave = nullptr; // pinned: [0] error flag of the last fused sweep,
-                                   // [1] non-finite flag of the last checked input
+    unsigned *host_flag = nullptr; // pinned: non-finite flag of the last checked input
     unsigned *d_check = nullptr;   // device flag: a checked input held a non-finite value
     // defect-correction solve (allocated at the first solve that needs them)
     void *Wb = nullptr;            // mixed: bf16 [8][S] face weights by red end
@@ -99,9 +58,7 @@ struct seg4d {
     float *gh_prev = nullptr, *gh_now = nullptr;
     bool has_ghost = false;
     Ghost ghost{};
-    int wave_T = 0;                // tiles per frame of the fused sweep
     int num_sms = 0;
-    int wave_occ = 1;              // occupancy limit of the fused sweep (CTAs per SM)
     SeedDev *seeds_d = nullptr;
     SeedStat *stat_d = nullptr;
     int nseeds = 0;
@@ -229,9 +186,8 @@ void free_all(seg4d *h)
     if (!h->lean) cudaFree(h->stage);
     cudaFree(h->partials);
     cudaFree(h->scal);
-    cudaFree(h->wave_ctrl);
     cudaFree(h->d_check);
-    if (h->host_wave) cudaFreeHost(h->host_wave);
+    if (h->host_flag) cudaFreeHost(h->host_flag);
     cudaFree(h->Wb);
     cudaFree(h->gb);
     cudaFree(h->ib);
@@ -353,7 +309,6 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
     bool timed_batch = false;
     int batch = check_every;
     CheckState cs;
-    bool wave_pending = false;
     for (;;) {
         const int nrec = launch_defect(L, x, h->beta, h->gamma, h->diag, h->W, h->ib, h->rho,
                                        h->dlt, h->partials, h->partials + 3 * kPartCap,
@@ -363,12 +318,6 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
         // scal[3..6] = sum r^2, min u, max u, max |r|
         if ((st = reduce_into(h, 3, nrec, true))) return st;
         if ((st = fetch_scal(h))) return st;
-        if (wave_pending) {
-            wave_pending = false;
-            if (h->host_wave[0] != 0u)
-                return fail(h, SEG4D_ERR_TIMEOUT,
-                            "fused sweep: a bounded wait between CTAs expired; u is not valid");
-        }
         if (timed_batch) {   // the batch before this check has completed
             float ms = 0.0f;
             if (cudaEventElapsedTime(&ms, h->evs0, h->evs1) == cudaSuccess) h->sweep_ms += ms;
@@ -400,14 +349,6 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
             }
             h->launches += 2LL * n;
             h->sweep_launches += 2LL * n;
-        } else if (h->p.sweep_variant == 0) {
-            CK(cudaMemsetAsync(h->wave_ctrl, 0, (4 + h->wave_T) * sizeof(unsigned), h->stream));
-            const int per_sm = std::min(h->p.ctas_per_sm > 0 ? h->p.ctas_per_sm : 4, h->wave_occ);
-            launch_sweep_wave(L, n, h->dlt, h->rho, h->lean ? h->gamma : nullptr,
-                              h->lean ? h->W : h->Ws, (float)omega, h->wave_ctrl,
-                              per_sm * h->num_sms, h->p.wait_test, h->stream);
-            h->launches += 1;
-            h->sweep_launches += 1;
         } else {
             const float *gam = h->lean ? h->gamma : nullptr;
             const float *wts = h->lean ? h->W : h->Ws;
@@ -428,12 +369,6 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
         CK_LAUNCH("apply");
         timed_batch = true;
         it += n;
-        if (!mixed && h->p.sweep_variant == 0) {
-            // the flag is read after the next check's synchronisation
-            CK(cudaMemcpyAsync(h->host_wave, h->wave_ctrl + 2, sizeof(unsigned),
-                               cudaMemcpyDeviceToHost, h->stream));
-            wave_pending = true;
-        }
     }
 }
 
@@ -626,7 +561,7 @@ seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
 }
 
 // check_finite: the split kernel flags non-finite values; the flag lands in
-// host_wave[1] once the stream has reached this point
+// host_flag[0] once the stream has reached this point
 seg4d_status copy_in(seg4d *h, const float *src, size_t n, int on_device, float *dst_split,
                      bool check_finite = false)
 {
@@ -643,7 +578,7 @@ seg4d_status copy_in(seg4d *h, const float *src, size_t n, int on_device, float 
     h->launches += 1;
     CK_LAUNCH("split");
     if (check_finite)
-        CK(cudaMemcpyAsync(h->host_wave + 1, h->d_check, sizeof(unsigned), cudaMemcpyDeviceToHost,
+        CK(cudaMemcpyAsync(h->host_flag, h->d_check, sizeof(unsigned), cudaMemcpyDeviceToHost,
                            h->stream));
     return SEG4D_OK;
 }
@@ -768,7 +703,6 @@ seg4d_status seg4d_create_ex(const seg4d_dims *dims, void *cuda_stream, int flag
         {(void **)&h->owner, 2 * S * 4},
         {(void **)&h->partials, 4 * kPartCap * sizeof(double)},
         {(void **)&h->scal, 8 * sizeof(double)},
-        {(void **)&h->wave_ctrl, (4 + (size_t)wave_tiles(L)) * sizeof(unsigned)},
         {(void **)&h->d_check, 4 * sizeof(unsigned)},
     };
     if (h->lean) {
@@ -804,12 +738,10 @@ seg4d_status seg4d_create_ex(const seg4d_dims *dims, void *cuda_stream, int flag
         h->stage = h->rho;   // 2S >= n1 n2 n3 n4 floats
         h->I0 = h->G;        // plane 0 of G until the set-up computes G
     }
-    h->wave_T = wave_tiles(L);
-    h->wave_occ = wave_max_ctas_per_sm();
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (h->num_sms < 1) h->num_sms = 1;
     if (cudaMallocHost(&h->host_scal, 8 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&h->host_wave, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost(&h->host_flag, 4 * sizeof(unsigned)) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
         cudaEventCreate(&h->evs0) != cudaSuccess || cudaEventCreate(&h->evs1) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -855,12 +787,9 @@ seg4d_status seg4d_set_params(seg4d *h, const seg4d_params *p)
         return fail(h, SEG4D_ERR_INVALID, "max_iters and check_every must be >= 1");
     if (p->precision != 0 && p->precision != 1)
         return fail(h, SEG4D_ERR_INVALID, "precision must be 0 or 1");
-    if (p->sweep_variant != 0 && p->sweep_variant != 1)
-        return fail(h, SEG4D_ERR_INVALID, "sweep_variant must be 0 or 1");
-    if (p->ctas_per_sm < 0 || p->ctas_per_sm > 64)
-        return fail(h, SEG4D_ERR_INVALID, "ctas_per_sm must lie in [0, 64]");
-    if (p->wait_test != 0 && p->wait_test != 1)
-        return fail(h, SEG4D_ERR_INVALID, "wait_test must be 0 or 1");
+    if (p->sweep_variant != 1 || p->ctas_per_sm != 0 || p->wait_test != 0)
+        return fail(h, SEG4D_ERR_INVALID,
+                    "sweep_variant must be 1, ctas_per_sm and wait_test 0 (reserved)");
     const bool geom = std::memcmp(p->h, h->p.h, sizeof(p->h)) != 0 || p->K != h->p.K ||
                       p->delta != h->p.delta || p->vartheta != h->p.vartheta ||
                       p->lambda_th != h->p.lambda_th || p->r_ball != h->p.r_ball ||
@@ -879,7 +808,7 @@ seg4d_status seg4d_set_image(seg4d *h, const float *I0, size_t n, int on_device)
     if (h->lean) h->I0 = h->G;
     if ((st = copy_in(h, I0, n, on_device, h->I0, true))) return st;
     CK(cudaStreamSynchronize(h->stream));
-    if (h->host_wave[1] != 0u) {   // the copy overwrote the old image
+    if (h->host_flag[0] != 0u) {   // the copy overwrote the old image
         h->has_image = false;
         h->setup_dirty = true;
         return fail(h, SEG4D_ERR_INVALID, "image has NaN/Inf; the handle has no image now");

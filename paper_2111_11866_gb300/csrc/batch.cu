@@ -13,11 +13,12 @@
 // its window by binary search in a short table of tile offsets, then runs
 // the same per-voxel code as the single-grid kernels (stencil.cuh).
 //
-// Every window keeps its own stopping test (||b - A u||_2 <= tol ||b||_2 with
-// FP64 sums reduced per window in a fixed order) on a fixed schedule (every
-// check_every sweeps).  A window's iterates therefore depend on nothing but
-// the window itself: its result is the same, bit for bit, alone or in any
-// mix of other windows.
+// Every window keeps its own stopping test (the single-grid rule: the
+// residual's 2-norm and its largest entry, FP64 sums reduced per window in a
+// fixed order), decided on the device, on its own schedule predicted from
+// its own residuals and rounded to a fixed grid of sweeps.  A window's
+// iterates therefore depend on nothing but the window itself: its result is
+// the same, bit for bit, alone or in any mix of other windows.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -118,30 +119,6 @@ __device__ inline bool group_pos(const BWin &wd, long long t, RowPos &rp, int &s
 }
 
 // --------------------------------------------------------------- kernels
-
-// One colour of one sweep of the correction system over every window, N
-// voxels per thread (relax_vec): delta <- delta + omega (rho + g sum_f w_f
-// delta_nb - delta) with FP32 weights and g = c/D, or BF16 weights and
-// g = c/D_b (mixed).  The black pass takes the tiles in reverse, starting on
-// what is still in L2.
-template <int C, bool kMixed, int N = kMixed ? kVecBF16 : kVecF32>
-__global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_bsweep(
-    const BWin *__restrict__ wins, const long long *__restrict__ starts, int nwin, float omega)
-{
-    const long long b = C ? (long long)gridDim.x - 1 - blockIdx.x : blockIdx.x;
-    const int w = find_win(starts, nwin, b);
-    const Layout L = wins[w].L;
-    RowPos rp{0, 0, 0, 0};
-    int s0 = 0, row = 0;
-    bool act = group_pos<N>(wins[w], b - starts[w], rp, s0, row);
-    act = act && 2 * s0 + (C ^ rp.p) < L.n1;
-    if (kMixed)
-        relax_vec<C, __nv_bfloat16, N>(L, wins[w].dlt, wins[w].rho, wins[w].gb, wins[w].Wb, omega,
-                                       act, row, s0, rp);
-    else
-        relax_vec<C, float, N>(L, wins[w].dlt, wins[w].rho, wins[w].gamma, wins[w].W, omega, act,
-                               row, s0, rp);
-}
 
 // per-window fixed-order reduction of the chunk records (one block per
 // window) into out[4 w .. 4 w + 2]; with amax (the defect pass's per-chunk
@@ -293,29 +270,23 @@ __global__ void __launch_bounds__(256) k_bmixed_prepare(const BWin *__restrict__
     }
 }
 
-// exact residual in flux form (flux_residual_vec; records, and max |r| of the
-// chunk in amax) + rho = r * ib, delta = 0; beta holds b itself.  A chunk of
-// kChunkTiles 256-slot tiles is kChunkTiles / N tiles of 256 N-slot groups.
-__global__ void __launch_bounds__(256, 2) k_bdefect(const BWin *__restrict__ wins,
-                                                    const long long *__restrict__ cstarts,
-                                                    int nwin, double *__restrict__ parts,
-                                                    double *__restrict__ amax)
+// Exact residual in flux form (flux_residual_vec) of the voxels of chunk c
+// of window wd (kChunkTiles / N tiles of 256 N-slot groups), with rho =
+// r * ib and delta = 0 (beta holds b itself): adds to the chunk's record a
+// (sum r^2, min u, max u) and max |r| ra.
+__device__ __forceinline__ void bdefect_chunk(const BWin &wd, long long c, Rec3f &a, float &ra)
 {
     constexpr int N = kVecF32;
-    const long long b = blockIdx.x;
-    const int w = find_win(cstarts, nwin, b);
-    const Layout L = wins[w].L;
-    const float *x = wins[w].x, *beta = wins[w].beta, *gamma = wins[w].gamma;
-    const float *diag = wins[w].diag, *W = wins[w].W, *ib = wins[w].ib;
-    float *rho = wins[w].rho, *dlt = wins[w].dlt;
+    const Layout L = wd.L;
+    const float *x = wd.x, *beta = wd.beta, *gamma = wd.gamma;
+    const float *diag = wd.diag, *W = wd.W, *ib = wd.ib;
+    float *rho = wd.rho, *dlt = wd.dlt;
     const long long nt = win_gtiles(L, N);
-    const long long t0 = (b - cstarts[w]) * (kChunkTiles / N);
-    Rec3f a = rec3f_init();
-    float ra = 0.0f;
+    const long long t0 = c * (kChunkTiles / N);
     for (long long t = t0; t < t0 + kChunkTiles / N && t < nt; ++t) {
         RowPos rp{0, 0, 0, 0};
         int s0 = 0, row = 0;
-        const bool in_win = group_pos<N>(wins[w], t, rp, s0, row);
+        const bool in_win = group_pos<N>(wd, t, rp, s0, row);
         for (int C = 0; C < 2; ++C) {
             const bool act = in_win && 2 * s0 + (C ^ rp.p) < L.n1;
             const long long q = (long long)row * L.P + s0 + (C ? L.S : 0);
@@ -346,24 +317,8 @@ __global__ void __launch_bounds__(256, 2) k_bdefect(const BWin *__restrict__ win
             stv<N>(dlt + q, zero);
         }
     }
-    block_write3(rec3f_acc(a), parts + 3 * b);
-    block_write_max(ra, amax + b);
 }
 
-// x <- x + delta on every slot of the tile (padding holds 0 in both)
-__global__ void __launch_bounds__(256) k_bapply(const BWin *__restrict__ wins,
-                                                const long long *__restrict__ starts, int nwin)
-{
-    const long long b = blockIdx.x;
-    const int w = find_win(starts, nwin, b);
-    const long long e = (b - starts[w]) * 256 + threadIdx.x;
-    const long long S = wins[w].L.S;
-    if (e >= S) return;
-    float *x = wins[w].x;
-    const float *d = wins[w].dlt;
-    x[e] += d[e];
-    x[S + e] += d[S + e];
-}
 
 __device__ inline double bseed_d2(const SeedDev &sd, int i, int j, int k)
 {
@@ -371,6 +326,236 @@ __device__ inline double bseed_d2(const SeedDev &sd, int i, int j, int k)
     const double dy = __dsub_rn((double)j, sd.y);
     const double dz = __dsub_rn((double)k, sd.z);
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// ----------------------------------------- solves with device-side checks
+//
+// A solve of many windows runs in rounds of kCheckGrid sweeps.  Every
+// window's tests fall on multiples of kCheckGrid sweeps, so in a round each
+// window still solving sweeps kCheckGrid times, and the windows whose test
+// is due at the round's end are tested: u += delta, the exact defect pass,
+// the per-window reduction and the decision (check_decision, the same rule
+// as the single-grid solve) -- all on the device.  The decision kernel also
+// builds the tables of the next round: the windows still solving (for the
+// sweeps) and those due at its end (for the tests), by position in the
+// solve's window array, with prefix offsets of their work units.  The host
+// only enqueues rounds and reads the count of windows still solving a few
+// rounds late, so a round costs no host synchronisation.  Each window's
+// arithmetic and schedule depend on nothing but its own residuals.
+
+enum { kSolveRun = 0, kSolveOk = 1, kSolveFail = 2 };
+
+struct BSolve {
+    double bnorm, bmax;   // ||b||_2 and max |b| of the window's system
+    double last_rel;      // ||r||_2 / ||b||_2 at its last test
+    CheckState cs;        // residual history of its tests
+    int next_check;       // sweep count of its next test (a multiple of kCheckGrid)
+    int state;            // kSolveRun, kSolveOk, kSolveFail
+    int iters;            // sweeps when it stopped
+    int fail;             // 1: max_iters reached, 2: residual not finite
+};
+
+// Work tables of a round (device): a list of window positions and, per
+// listed window, prefix offsets of its units (sweep groups, 256-slot tiles,
+// reduction chunks); n = listed windows.
+struct DevTabs {
+    int *act_idx;          // windows still solving
+    long long *act_pt;     // their sweep tiles (256 groups of N slots), prefix
+    int *act_n;
+    int *due_idx;          // windows due for a test at the round's end
+    long long *due_t;      // their 256-slot tiles, prefix
+    long long *due_c;      // their reduction chunks, prefix
+    int *due_n;
+    int *n_solving;        // windows still solving after the last decision
+};
+
+// Sweep of colour C over the windows still solving, grid-stride over their
+// sweep tiles (the black pass walks them backwards, starting on what the red
+// pass left in L2); the per-voxel work is k_bsweep's.
+template <int C, bool kMixed, int N = kMixed ? kVecBF16 : kVecF32>
+__global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_bsweep_dev(
+    const BWin *__restrict__ wins, DevTabs T, float omega)
+{
+    const int nw = *T.act_n;
+    const long long total = nw > 0 ? T.act_pt[nw] : 0;
+    for (long long g = blockIdx.x; g < total; g += gridDim.x) {
+        const long long b = C ? total - 1 - g : g;
+        const int i = find_win(T.act_pt, nw, b);
+        const BWin &wd = wins[T.act_idx[i]];
+        const Layout L = wd.L;
+        RowPos rp{0, 0, 0, 0};
+        int s0 = 0, row = 0;
+        bool act = group_pos<N>(wd, b - T.act_pt[i], rp, s0, row);
+        act = act && 2 * s0 + (C ^ rp.p) < L.n1;
+        if (kMixed)
+            relax_vec<C, __nv_bfloat16, N>(L, wd.dlt, wd.rho, wd.gb, wd.Wb, omega, act, row, s0,
+                                           rp);
+        else
+            relax_vec<C, float, N>(L, wd.dlt, wd.rho, wd.gamma, wd.W, omega, act, row, s0, rp);
+    }
+}
+
+// x <- x + delta over the windows due for a test
+__global__ void __launch_bounds__(256) k_bapply_dev(const BWin *__restrict__ wins, DevTabs T)
+{
+    const int nw = *T.due_n;
+    const long long total = nw > 0 ? T.due_t[nw] : 0;
+    for (long long b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = find_win(T.due_t, nw, b);
+        const BWin &wd = wins[T.due_idx[i]];
+        const long long e = (b - T.due_t[i]) * 256 + threadIdx.x;
+        const long long S = wd.L.S;
+        if (e >= S) continue;
+        float *x = wd.x;
+        const float *d = wd.dlt;
+        x[e] += d[e];
+        x[S + e] += d[S + e];
+    }
+}
+
+// exact defect pass over the windows due for a test, grid-stride over their
+// reduction chunks: one record (sum r^2, min u, max u) and one max |r| per
+// chunk, numbered in the due table's chunk order
+__global__ void __launch_bounds__(256, 2) k_bdefect_dev(const BWin *__restrict__ wins, DevTabs T,
+                                                        double *__restrict__ parts,
+                                                        double *__restrict__ amax)
+{
+    const int nw = *T.due_n;
+    const long long total = nw > 0 ? T.due_c[nw] : 0;
+    for (long long b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = find_win(T.due_c, nw, b);
+        Rec3f a = rec3f_init();
+        float ra = 0.0f;
+        bdefect_chunk(wins[T.due_idx[i]], b - T.due_c[i], a, ra);
+        block_write3(rec3f_acc(a), parts + 3 * b);
+        block_write_max(ra, amax + b);
+        __syncthreads();   // the record helpers' shared memory is reused next
+    }
+}
+
+// per due window (block i): fixed-order reduction of its chunk records into
+// out[4 i .. 4 i + 3] = (sum r^2, min u, max u, max |r|)
+__global__ void __launch_bounds__(256) k_breduce_dev(DevTabs T, const double *__restrict__ parts,
+                                                     const double *__restrict__ amax,
+                                                     double *__restrict__ out)
+{
+    const int i = blockIdx.x;
+    if (i >= *T.due_n) return;
+    Acc3 a{0.0, DBL_MAX, -DBL_MAX};
+    float m = 0.0f;
+    for (long long c = T.due_c[i] + threadIdx.x; c < T.due_c[i + 1]; c += blockDim.x) {
+        a = acc3_merge(a, Acc3{parts[3 * c], parts[3 * c + 1], parts[3 * c + 2]});
+        m = fmaxf(m, (float)amax[c]);
+    }
+    block_write3(a, out + 4 * i);
+    block_write_max(m, out + 4 * i + 3);
+}
+
+struct DecideConst {
+    double tol, tol_inf;
+    int check_every, max_iters, mixed, K;
+};
+
+// Block-wide exclusive prefix sum (1024 threads at most); *total gets the
+// block's sum.  Every thread calls it.
+__device__ inline long long block_scan_excl(long long v, long long *total)
+{
+    __shared__ long long ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        long long s = lane < nw ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) ws[lane] = s;   // inclusive sums of the warps
+    }
+    __syncthreads();
+    const long long before = (wid > 0 ? ws[wid - 1] : 0) + x - v;
+    *total = ws[nw - 1];
+    __syncthreads();
+    return before;
+}
+
+// One block: the decisions of the windows due at sweep count `it`, then the
+// tables of the next round (windows still solving; those of them whose test
+// falls at it + K).  cnt: per window of the solve, its sweep tiles, 256-slot
+// tiles and reduction chunks ([3][nsolve]).
+__global__ void __launch_bounds__(1024) k_bdecide(BSolve *__restrict__ sw, int nsolve,
+                                                  const double *__restrict__ out, int it,
+                                                  DecideConst P,
+                                                  const long long *__restrict__ cnt, DevTabs T)
+{
+    const int nd = *T.due_n;
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+        BSolve &s = sw[T.due_idx[i]];
+        const double rn = sqrt(out[4 * i]);
+        const double rinf = out[4 * i + 3];
+        s.last_rel = s.bnorm > 0.0 ? rn / s.bnorm : rn;
+        if (!isfinite(rn)) {
+            s.state = kSolveFail;
+            s.fail = 2;
+            s.iters = it;
+            continue;
+        }
+        int n = P.check_every;
+        const int dec = check_decision(s.cs, rn, s.bnorm, rinf, s.bmax, it, P.tol, P.tol_inf,
+                                       P.check_every, P.mixed != 0, n);
+        if (dec != kGoOn) {
+            s.state = kSolveOk;
+            s.iters = it;
+        } else if (it >= P.max_iters) {
+            s.state = kSolveFail;
+            s.fail = 1;
+            s.iters = it;
+        } else {
+            s.next_check = (it + n + P.K - 1) / P.K * P.K;
+        }
+    }
+    __syncthreads();
+    __shared__ long long run[5];   // running (solving, due, sweep tiles, tiles, chunks)
+    if (threadIdx.x < 5) run[threadIdx.x] = 0;
+    __syncthreads();
+    for (int base = 0; base < nsolve; base += blockDim.x) {
+        const int w = base + (int)threadIdx.x;
+        const bool act = w < nsolve && sw[w].state == kSolveRun;
+        const bool due = act && sw[w].next_check == it + P.K;
+        long long tot[5];
+        const long long oa = block_scan_excl(act ? 1 : 0, &tot[0]);
+        const long long od = block_scan_excl(due ? 1 : 0, &tot[1]);
+        const long long op = block_scan_excl(act ? cnt[w] : 0, &tot[2]);
+        const long long ot = block_scan_excl(due ? cnt[nsolve + w] : 0, &tot[3]);
+        const long long oc = block_scan_excl(due ? cnt[2 * nsolve + w] : 0, &tot[4]);
+        if (act) {
+            T.act_idx[run[0] + oa] = w;
+            T.act_pt[run[0] + oa] = run[2] + op;
+        }
+        if (due) {
+            T.due_idx[run[1] + od] = w;
+            T.due_t[run[1] + od] = run[3] + ot;
+            T.due_c[run[1] + od] = run[4] + oc;
+        }
+        __syncthreads();
+        if (threadIdx.x < 5) run[threadIdx.x] += tot[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        T.act_pt[run[0]] = run[2];
+        T.due_t[run[1]] = run[3];
+        T.due_c[run[1]] = run[4];
+        *T.act_n = (int)run[0];
+        *T.due_n = (int)run[1];
+        *T.n_solving = (int)run[0];
+    }
 }
 
 // per (window, seed) block: min/max of u over the ball (Eq. 841), then the
@@ -570,6 +755,16 @@ struct seg4d_batch {
     long long launches = 0;
     double sweep_ms = 0.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // solves with device-side checks (batch_solve): per-window state, unit
+    // counts, the round tables and their staging, the count of windows still
+    // solving read back a few rounds late
+    int num_sms = 0;
+    BSolve *d_sw = nullptr, *h_sw = nullptr;
+    long long *d_cnt = nullptr, *h_cnt = nullptr;        // [3][max_windows]
+    int *d_tab_int = nullptr, *h_tab_int = nullptr;      // act_idx, due_idx, act_n, due_n, n
+    long long *d_tab_ll = nullptr, *h_tab_ll = nullptr;  // act_pt, due_t, due_c
+    int *h_nsolv = nullptr;
+    cudaEvent_t ev_round[3] = {}, ev_s0[3] = {}, ev_s1[3] = {};
     std::string err;
 };
 
@@ -761,122 +956,127 @@ struct SolveItem {
 
 // Batched red-black SOR over every window of `items` (each window's d.x,
 // beta = b, gamma, diag, W, ib already set up), as defect correction (see
-// solve_system in api.cu): a test is the exact flux-form residual, which
-// also sets up the correction system; the sweeps solve it for delta, and
-// u += delta precedes the next test.  Per window: stop when
+// solve_system in api.cu), in rounds of kCheckGrid sweeps with the tests
+// decided on the device (k_bdecide).  A window stops on its own residuals:
 // ||b - A x|| <= tol ||b|| and, with tol_inf > 0, max |b - A x| <= tol_inf
-// max |b| (the per-voxel part, as in the single-grid solve).  Each window
-// has its own check schedule
-// (next_check_batch on its own residual history): every round sweeps all
-// active windows up to the earliest pending check, then tests the windows
-// whose check is due (u += delta, then the defect pass, for those only).  A window's sweeps and tests therefore do not depend on
-// the other windows, and its result is the same alone or in any mix.
+// max |b| (or max |r| at its FP32 floor), exactly as the single-grid solve
+// decides; its tests fall on multiples of kCheckGrid sweeps (max_iters is
+// honoured to that grid).  Nothing a window computes depends on the other
+// windows, so its result is the same alone or in any mix.
 seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double omega, double tol,
                          int max_iters, int check_every, long long &sweeps_total,
                          bool mixed = false, double tol_inf = 0.0)
 {
-    std::vector<SolveItem *> act, due;
-    for (auto &it : items) {
-        it.next_check = 0;
-        it.cs = CheckState{};
-        act.push_back(&it);
-    }
-    due = act;
-    int it = 0;
-    bool timed = false;
+    const int ns = (int)items.size();
+    if (ns == 0) return SEG4D_OK;
     seg4d_status st;
-    for (;;) {
-        // test the windows whose check is due at sweep `it`
-        std::vector<Window *> ws;
-        for (auto *a : due) ws.push_back(a->w);
-        if ((st = set_table(b, ws))) return st;
-        if (it > 0) {
-            k_bapply<<<(unsigned)b->n_tile, 256, 0, b->stream>>>(b->d_wins, b->d_tile,
-                                                                 (int)ws.size());
-            b->launches += 1;
-        }
-        const long long nch = b->n_chunk;
-        if ((st = ensure_parts(b, nch))) return st;
-        k_bdefect<<<(unsigned)nch, 256, 0, b->stream>>>(b->d_wins, b->d_chunk, (int)ws.size(),
-                                                        b->d_parts, b->d_parts + 3 * b->parts_cap);
-        b->launches += 1;
-        BCK(cudaGetLastError());
-        if ((st = reduce_windows(b, ws.size(), true))) return st;
-        if (timed) {
-            float ms = 0.0f;
-            if (cudaEventElapsedTime(&ms, b->e0, b->e1) == cudaSuccess) b->sweep_ms += ms;
-            timed = false;
-        }
-        for (size_t i = 0; i < due.size(); ++i) {
-            SolveItem *a = due[i];
-            const double rn = std::sqrt(b->h_out[4 * i]);
-            const double rinf = b->h_out[4 * i + 3];
-            a->w->last_res_rel = a->bnorm > 0 ? rn / a->bnorm : rn;
-            if (!std::isfinite(rn)) {
-                a->done = true;
-                a->ok = false;
-                a->w->err = "residual is not finite";
-            } else {
-                int n = check_every;
-                const int dec = check_decision(a->cs, rn, a->bnorm, rinf, a->bmax, it, tol,
-                                               tol_inf, check_every, mixed, n);
-                if (dec != kGoOn) {
-                    a->done = true;
-                    a->ok = true;
-                    a->iters = it;
-                } else if (it >= max_iters) {
-                    a->done = true;
-                    a->ok = false;
-                    a->iters = it;
-                    a->w->err = "solve reached max_iters";
+    std::vector<Window *> ws;
+    for (auto &it : items) ws.push_back(it.w);
+    if ((st = set_table(b, ws))) return st;   // d_wins holds the solve's windows
+    const int N = mixed ? kVecBF16 : kVecF32;
+    // per-window unit counts, initial state, and the first test table (every
+    // window is tested before its first sweep)
+    long long *cnt = b->h_cnt;
+    for (int i = 0; i < ns; ++i) {
+        cnt[i] = win_gtiles(ws[i]->L, N);
+        cnt[ns + i] = win_tiles(ws[i]->L);
+        cnt[2 * ns + i] = chunks_of(*ws[i]);
+        b->h_sw[i] = BSolve{items[i].bnorm, items[i].bmax, 0.0, CheckState{}, 0, kSolveRun, 0, 0};
+        b->h_tab_int[i] = i;   // due_idx
+    }
+    b->h_tab_int[ns] = ns;    // due_n
+    long long *ht = b->h_tab_ll;   // due_t then due_c
+    ht[0] = 0;
+    ht[ns + 1] = 0;
+    for (int i = 0; i < ns; ++i) {
+        ht[i + 1] = ht[i] + cnt[ns + i];
+        ht[ns + 2 + i] = ht[ns + 1 + i] + cnt[2 * ns + i];
+    }
+    const long long all_chunks = ht[2 * ns + 1];
+    if ((st = ensure_parts(b, all_chunks))) return st;
+    const int cap = b->max_windows;
+    DevTabs T;
+    T.act_idx = b->d_tab_int;
+    T.due_idx = b->d_tab_int + cap;
+    T.act_n = b->d_tab_int + 2 * cap;
+    T.due_n = b->d_tab_int + 2 * cap + 1;
+    T.n_solving = b->d_tab_int + 2 * cap + 2;
+    T.act_pt = b->d_tab_ll;
+    T.due_t = b->d_tab_ll + (cap + 1);
+    T.due_c = b->d_tab_ll + 2 * (cap + 1);
+    BCK(cudaMemcpyAsync(b->d_cnt, cnt, 3 * ns * sizeof(long long), cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaMemcpyAsync(b->d_sw, b->h_sw, ns * sizeof(BSolve), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemcpyAsync(T.due_idx, b->h_tab_int, ns * sizeof(int), cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaMemcpyAsync(T.due_n, b->h_tab_int + ns, sizeof(int), cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaMemcpyAsync(T.due_t, ht, (ns + 1) * sizeof(long long), cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaMemcpyAsync(T.due_c, ht + ns + 1, (ns + 1) * sizeof(long long),
+                        cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemsetAsync(T.act_n, 0, sizeof(int), b->stream));
+    const DecideConst P{tol, tol_inf, check_every, max_iters, mixed ? 1 : 0, kCheckGrid};
+    double *amax = b->d_parts + 3 * b->parts_cap;
+    const int sms = b->num_sms;
+    const unsigned g_sweep = (unsigned)(sms * (N == 2 ? SEG4D_VEC2_MINB : SEG4D_VEC4_MINB));
+    const unsigned g_apply = (unsigned)(sms * 8), g_defect = (unsigned)(sms * 2);
+    // the host runs at most kLag rounds ahead of the last count it has read
+    constexpr int kLag = 3;
+    for (int r = 0;; ++r) {
+        const int slot = r % kLag;
+        if (r > 0) {
+            BCK(cudaEventRecord(b->ev_s0[slot], b->stream));
+            for (int s = 0; s < kCheckGrid; ++s) {
+                if (mixed) {
+                    k_bsweep_dev<0, true><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T,
+                                                                          (float)omega);
+                    k_bsweep_dev<1, true><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T,
+                                                                          (float)omega);
                 } else {
-                    // checks land on multiples of kCheckGrid sweeps, so that the
-                    // windows' own schedules meet in fewer rounds (each round
-                    // costs a defect pass, a reduction and a host wait); the grid
-                    // is fixed, so a window's schedule still depends on nothing
-                    // but its own residuals
-                    const int nc = (it + n + kCheckGrid - 1) / kCheckGrid * kCheckGrid;
-                    a->next_check = std::min(nc, max_iters);
+                    k_bsweep_dev<0, false><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T,
+                                                                           (float)omega);
+                    k_bsweep_dev<1, false><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T,
+                                                                           (float)omega);
                 }
             }
+            BCK(cudaEventRecord(b->ev_s1[slot], b->stream));
+            k_bapply_dev<<<g_apply, 256, 0, b->stream>>>(b->d_wins, T);
+            b->launches += 2LL * kCheckGrid + 1;
         }
-        std::vector<SolveItem *> next;
-        for (auto *a : act)
-            if (!a->done) next.push_back(a);
-        act.swap(next);
-        if (act.empty()) break;
-        // sweep every active window up to the earliest pending check
-        int until = max_iters;
-        for (auto *a : act) until = std::min(until, a->next_check);
-        const int n = until - it;
-        ws.clear();
-        for (auto *a : act) ws.push_back(a->w);
-        if ((st = set_table(b, ws))) return st;
-        BCK(cudaEventRecord(b->e0, b->stream));
-        const long long nptiles = b->n_ptile;
-        const int nw = (int)ws.size();
-        for (int s = 0; s < n; ++s) {
-            if (mixed) {
-                k_bsweep<0, true><<<(unsigned)nptiles, 256, 0, b->stream>>>(b->d_wins, b->d_ptile,
-                                                                            nw, (float)omega);
-                k_bsweep<1, true><<<(unsigned)nptiles, 256, 0, b->stream>>>(b->d_wins, b->d_ptile,
-                                                                            nw, (float)omega);
-            } else {
-                k_bsweep<0, false><<<(unsigned)nptiles, 256, 0, b->stream>>>(
-                    b->d_wins, b->d_ptile, nw, (float)omega);
-                k_bsweep<1, false><<<(unsigned)nptiles, 256, 0, b->stream>>>(
-                    b->d_wins, b->d_ptile, nw, (float)omega);
-            }
-        }
-        b->launches += 2LL * n;
+        k_bdefect_dev<<<g_defect, 256, 0, b->stream>>>(b->d_wins, T, b->d_parts, amax);
+        k_breduce_dev<<<(unsigned)ns, 256, 0, b->stream>>>(T, b->d_parts, amax, b->d_out);
+        k_bdecide<<<1, 1024, 0, b->stream>>>(b->d_sw, ns, b->d_out, r * kCheckGrid, P, b->d_cnt,
+                                             T);
+        b->launches += 3;
         BCK(cudaGetLastError());
-        BCK(cudaEventRecord(b->e1, b->stream));
-        timed = true;
-        sweeps_total += (long long)n * (long long)act.size();
-        it = until;
-        due.clear();
-        for (auto *a : act)
-            if (a->next_check == it) due.push_back(a);
+        BCK(cudaMemcpyAsync(b->h_nsolv + slot, T.n_solving, sizeof(int), cudaMemcpyDeviceToHost,
+                            b->stream));
+        BCK(cudaEventRecord(b->ev_round[slot], b->stream));
+        const int q = r - (kLag - 1);   // the oldest round in flight
+        if (q >= 0) {
+            const int qs = q % kLag;
+            BCK(cudaEventSynchronize(b->ev_round[qs]));
+            if (q > 0) {
+                float ms = 0.0f;
+                if (cudaEventElapsedTime(&ms, b->ev_s0[qs], b->ev_s1[qs]) == cudaSuccess)
+                    b->sweep_ms += ms;
+            }
+            if (b->h_nsolv[qs] == 0) break;
+        }
+    }
+    BCK(cudaMemcpyAsync(b->h_sw, b->d_sw, ns * sizeof(BSolve), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < ns; ++i) {
+        const BSolve &s = b->h_sw[i];
+        SolveItem &a = items[i];
+        a.done = true;
+        a.ok = s.state == kSolveOk;
+        a.iters = s.iters;
+        a.w->last_res_rel = s.last_rel;
+        if (s.state == kSolveFail)
+            a.w->err = s.fail == 2 ? "residual is not finite" : "solve reached max_iters";
+        sweeps_total += s.iters;
     }
     return SEG4D_OK;
 }
@@ -1086,6 +1286,20 @@ void batch_free(seg4d_batch *b)
     if (b->h_out) cudaFreeHost(b->h_out);
     if (b->e0) cudaEventDestroy(b->e0);
     if (b->e1) cudaEventDestroy(b->e1);
+    cudaFree(b->d_sw);
+    cudaFree(b->d_cnt);
+    cudaFree(b->d_tab_int);
+    cudaFree(b->d_tab_ll);
+    if (b->h_sw) cudaFreeHost(b->h_sw);
+    if (b->h_cnt) cudaFreeHost(b->h_cnt);
+    if (b->h_tab_int) cudaFreeHost(b->h_tab_int);
+    if (b->h_tab_ll) cudaFreeHost(b->h_tab_ll);
+    if (b->h_nsolv) cudaFreeHost(b->h_nsolv);
+    for (int k = 0; k < 3; ++k) {
+        if (b->ev_round[k]) cudaEventDestroy(b->ev_round[k]);
+        if (b->ev_s0[k]) cudaEventDestroy(b->ev_s0[k]);
+        if (b->ev_s1[k]) cudaEventDestroy(b->ev_s1[k]);
+    }
 }
 
 }  // namespace
@@ -1125,6 +1339,22 @@ seg4d_status seg4d_batch_create(size_t arena_bytes, int max_windows, void *cuda_
               cudaEventCreate(&b->ev_table) == cudaSuccess &&
               cudaMallocHost(&b->h_out, 4 * sizeof(double) * max_windows) == cudaSuccess &&
               cudaEventCreate(&b->e0) == cudaSuccess && cudaEventCreate(&b->e1) == cudaSuccess;
+    const size_t mw = (size_t)max_windows;
+    ok = ok && cudaMalloc(&b->d_sw, sizeof(BSolve) * mw) == cudaSuccess &&
+         cudaMallocHost(&b->h_sw, sizeof(BSolve) * mw) == cudaSuccess &&
+         cudaMalloc(&b->d_cnt, sizeof(long long) * 3 * mw) == cudaSuccess &&
+         cudaMallocHost(&b->h_cnt, sizeof(long long) * 3 * mw) == cudaSuccess &&
+         cudaMalloc(&b->d_tab_int, sizeof(int) * (2 * mw + 3)) == cudaSuccess &&
+         cudaMallocHost(&b->h_tab_int, sizeof(int) * (mw + 1)) == cudaSuccess &&
+         cudaMalloc(&b->d_tab_ll, sizeof(long long) * 3 * (mw + 1)) == cudaSuccess &&
+         cudaMallocHost(&b->h_tab_ll, sizeof(long long) * 2 * (mw + 1)) == cudaSuccess &&
+         cudaMallocHost(&b->h_nsolv, sizeof(int) * 3) == cudaSuccess &&
+         cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) ==
+             cudaSuccess;
+    for (int k = 0; ok && k < 3; ++k)
+        ok = cudaEventCreate(&b->ev_round[k]) == cudaSuccess &&
+             cudaEventCreate(&b->ev_s0[k]) == cudaSuccess &&
+             cudaEventCreate(&b->ev_s1[k]) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         batch_free(b);

@@ -22,6 +22,7 @@
 // coefficient kernel folds into D.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <cuda_runtime.h>
@@ -156,9 +157,6 @@ int launch_step_coef(const Layout &L, const float *u, const float *G, const doub
 // gamma = NULL: a unit-diagonal (scaled) system, G = 1
 void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,
                   const float *W, float omega, cudaStream_t st);
-void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta,
-                       const float *gamma, const float *W, float omega, unsigned *ctrl, int ctas,
-                       int test_wait, cudaStream_t st);
 // mixed precision (mixed_kernels.cu); Wb is a __nv_bfloat16 [8][S] array
 void launch_mixed_prepare(const Layout &L, const float *W, const float *gamma, const float *diag,
                           void *Wb, float *gb, float *ib, cudaStream_t st);
@@ -171,8 +169,6 @@ int launch_defect(const Layout &L, const float *u, const float *b, const float *
 void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *rho,
                         const float *gb, const void *Wb, float omega, cudaStream_t st);
 void launch_apply(const Layout &L, float *u, const float *delta, cudaStream_t st);
-int wave_tiles(const Layout &L);        // tiles per frame of the fused sweep
-int wave_max_ctas_per_sm();             // occupancy limit of the fused sweep
 // FP32 solves (see k_scaled_weights): scaled correction weights, per-voxel
 // r = sqrt(gamma) and 1 / (D r); and u <- u + r delta
 void launch_scaled_weights(const Layout &L, const float *W, float *Ws, const float *gamma,
@@ -196,8 +192,20 @@ void launch_reduce_partials(const double *partials, int nparts, double *out, cud
 // 1e-3.  Batches are kept in [max(1, check_every/4), 8*check_every]; without
 // two usable checks the batch is check_every.  The result depends only on the
 // solve's own residual history.
-int next_check_batch(double rn, double prev_rn, int it, int prev_it, double tol, double bnorm,
-                     int check_every, bool mixed);
+// (host and device: the batch engine decides its checks on the device)
+__host__ __device__ inline int next_check_batch(double rn, double prev_rn, int it, int prev_it,
+                                                double tol, double bnorm, int check_every,
+                                                bool mixed)
+{
+    if (!(prev_rn > 0.0 && rn < prev_rn && it > prev_it && rn > 0.0)) return check_every;
+    const double gain = mixed ? 1e-2 : 1e-3;
+    const double rho = pow(rn / prev_rn, 1.0 / (it - prev_it));
+    const double need = log(tol * bnorm / rn) / log(rho);
+    const double cap = log(gain) / log(rho);
+    const int lo = check_every / 4 > 1 ? check_every / 4 : 1, hi = 8 * check_every;
+    const double want = ceil(fmin(0.8 * need, cap));
+    return isfinite(want) ? (int)fmin((double)hi, fmax((double)lo, want)) : check_every;
+}
 
 // Stopping decision at a check of a solve.  The test has two parts:
 // ||r||_2 <= tol ||b||_2 and, with tol_inf > 0, max |r| <= tol_inf max |b|
@@ -215,8 +223,33 @@ struct CheckState {
     int prev_it = 0;
 };
 enum { kGoOn = 0, kStop = 1, kStopFloor = 2 };
-int check_decision(CheckState &cs, double rn, double bn, double rinf, double bmax, int it,
-                   double tol, double tol_inf, int check_every, bool mixed, int &batch);
+__host__ __device__ inline int check_decision(CheckState &cs, double rn, double bn, double rinf,
+                                              double bmax, int it, double tol, double tol_inf,
+                                              int check_every, bool mixed, int &batch)
+{
+    const bool l2 = rn <= tol * bn;
+    const bool inf = tol_inf <= 0.0 || rinf <= tol_inf * bmax;
+    int res = kGoOn;
+    if (l2 && inf) {
+        res = kStop;
+    } else if (l2 && cs.prev_inf > 0.0 && it - cs.prev_it >= check_every) {
+        const double rho = pow(rinf / cs.prev_inf, 1.0 / (it - cs.prev_it));
+        if (!(rho < 0.99)) res = kStopFloor;
+    }
+    if (res == kGoOn) {
+        if (l2) {
+            const int n = next_check_batch(rinf, cs.prev_inf, it, cs.prev_it, tol_inf, bmax,
+                                           check_every, mixed);
+            batch = n > check_every ? n : check_every;
+        } else {
+            batch = next_check_batch(rn, cs.prev_rn, it, cs.prev_it, tol, bn, check_every, mixed);
+        }
+    }
+    cs.prev_rn = rn;
+    cs.prev_inf = rinf;
+    cs.prev_it = it;
+    return res;
+}
 
 // message of the last failed handle-free call of this thread (api.cu)
 std::string &handle_free_error();

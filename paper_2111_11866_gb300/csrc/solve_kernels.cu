@@ -76,253 +76,6 @@ void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *
                                                (const __nv_bfloat16 *)Wb, omega, st);
 }
 
-// ------------------------------------------ fused red-black frame pipeline
-
-// One launch performs `nsweeps` complete red-black sweeps as a pipeline over
-// the frame axis l, so that on grids whose frames are small against L2 the
-// face weights of a frame come from DRAM once per sweep: its red pass loads
-// them and the black pass two frame-steps later finds them in L2 (the
-// per-colour launches read them twice).
-//
-// Work item (g, T): frame-step g, tile T of a frame.  A tile is TS
-// consecutive row-chunks (64 slots of one row) of one z-plane k; tiles of a
-// plane are numbered tt = 0..tpp-1 and T = k tpp + tt.  Step g of sweep q =
-// g div Ts (Ts = max(n4, 4) steps per sweep) relaxes the RED voxels of frame
-// s = g mod Ts (if s < n4) on warps 0-3 and, on warps 4-7 at the same time,
-// the BLACK voxels of the frame f whose red pass ran at step g-2.  Red of
-// frame s reads black of frames s-1, s, s+1 before this sweep updates them
-// (their black steps come later) and after the previous sweep did (Ts >= 4);
-// black of frame f reads red of frames f-1, f, f+1 after this sweep's update.
-// So the result is that of all-red-then-all-black sweeps, bit for bit (the
-// per-voxel arithmetic is relax_vec's, the same as the per-colour kernels).
-//
-// Scheduling: CTAs take items in ticket order (g-major).  Every read and
-// overwrite above is covered by: item (g, T) starts once tile T has
-// completed step g-1 and its neighbour tiles (T+-1 in the plane, T+-tpp in
-// the neighbouring planes) have completed step g-2 (done[t] counts completed
-// steps of tile t).  Waits only ever point at smaller tickets, which running
-// CTAs hold, so the schedule cannot deadlock.  Every wait is bounded
-// (kWaveTimeoutNs on the global timer): on expiry the CTA raises ctrl[2]
-// (error) and ctrl[1] (abort) and all CTAs leave; the host reports
-// SEG4D_ERR_TIMEOUT.
-//
-// Visibility: an item's stores are published by one thread after the CTA
-// barrier, with a gpu-scope fence and a release store of done[T].  The next
-// CTA acquires each counter it depends on (ld.acquire.gpu) before its own
-// barrier, so every thread's later plain loads, L1 included, see the stores
-// (release -> acquire -> barrier orders them in the PTX memory model).
-//
-// ctrl layout (u32, zeroed before every launch): [0] ticket, [1] abort,
-// [2] error, [3] flag of the timeout test hook (never set), [4 ..] done[Tf].
-#ifndef SEG4D_WAVE_PASS
-#define SEG4D_WAVE_PASS 4
-#endif
-#ifndef SEG4D_WAVE_MINB
-#define SEG4D_WAVE_MINB 3
-#endif
-constexpr int kWaveWarps = 8;                 // 4 red + 4 black warps per CTA
-constexpr int kWaveGroup = 32 * kVecF32;      // slots of a row-chunk (one warp)
-constexpr unsigned long long kWaveTimeoutNs = 2000000000ull;
-
-// Tiling of the fused sweep (host and device agree through this struct).
-struct WaveGeo {
-    int nch;        // row-chunks per row, ceil(P / kWaveGroup)
-    int npass;      // row-chunks a warp relaxes per item (>= nch / 4)
-    int TS;         // row-chunks per tile = 4 npass
-    int tpp;        // tiles per z-plane
-    int Tf;         // tiles per frame = tpp n3
-    int Ts;         // frame-steps per sweep = max(n4, 4)
-    unsigned total; // items of the launch
-};
-
-static WaveGeo wave_geo(const Layout &L, int nsweeps)
-{
-    WaveGeo G;
-    G.nch = (L.P + kWaveGroup - 1) / kWaveGroup;
-    G.npass = std::max(SEG4D_WAVE_PASS, (G.nch + 3) / 4);
-    G.TS = 4 * G.npass;
-    G.tpp = (L.n2 * G.nch + G.TS - 1) / G.TS;
-    G.Tf = G.tpp * L.n3;
-    G.Ts = std::max(L.n4, 4);
-    G.total = (unsigned)(((long long)nsweeps * G.Ts + 2) * G.Tf);
-    return G;
-}
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
-{
-    return *(const volatile unsigned *)p;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Spin until *flag >= target; false if the abort flag rose or the bound ran
-// out (then error and abort are raised).
-__device__ bool wave_wait(const unsigned *flag, unsigned target, unsigned *ctrl,
-                          unsigned long long t0)
-{
-    while (ld_acquire_u32(flag) < target) {
-        if (ld_volatile_u32(&ctrl[1]) != 0u) return false;
-        if (global_ns() - t0 > kWaveTimeoutNs) {
-            atomicExch(&ctrl[2], 1u);
-            atomicExch(&ctrl[1], 1u);
-            return false;
-        }
-        __nanosleep(32);
-    }
-    return true;
-}
-
-// One colour of a tile: warp wi of the colour's four relaxes row-chunks
-// wi, wi + 4, ... of the tile (plane k, frame l) with relax_vec.
-template <int C, bool kUnit>
-__device__ __forceinline__ void wave_tile(const Layout &L, const WaveGeo &G, float *__restrict__ x,
-                                          const float *__restrict__ B,
-                                          const float *__restrict__ Gm,
-                                          const float *__restrict__ W, float omega, int tt, int k,
-                                          int l, int wi)
-{
-    const int lane = threadIdx.x & 31;
-    const int nrc = L.n2 * G.nch;
-    for (int ps = 0; ps < G.npass; ++ps) {
-        const int rc = tt * G.TS + 4 * ps + wi;
-        if (rc >= nrc) break;   // the whole warp
-        RowPos rp;
-        rp.j = rc / G.nch;
-        rp.k = k;
-        rp.l = l;
-        rp.p = (rp.j + k + l) & 1;
-        const int s0 = (rc - rp.j * G.nch) * kWaveGroup + kVecF32 * lane;
-        const bool act = s0 < L.P && 2 * s0 + (C ^ rp.p) < L.n1;
-        const int row = rp.j + L.n2 * (k + L.n3 * l);
-        relax_vec<C, float, kVecF32, kUnit>(L, x, B, Gm, W, omega, act, row, s0, rp);
-    }
-}
-
-template <bool kUnit>
-__global__ void __launch_bounds__(32 * kWaveWarps, SEG4D_WAVE_MINB) k_sweep_wave(
-    Layout L, WaveGeo G, float *__restrict__ x, const float *__restrict__ B,
-    const float *__restrict__ Gm, const float *__restrict__ W, float omega, int nsweeps,
-    unsigned *__restrict__ ctrl, int test_wait)
-{
-    __shared__ unsigned sh_ticket[2], sh_stop;
-    unsigned *done = ctrl + 4;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned Tf = (unsigned)G.Tf;
-    const unsigned red_steps = (unsigned)nsweeps * (unsigned)G.Ts;
-    if (threadIdx.x == 0) sh_ticket[0] = atomicAdd(&ctrl[0], 1u);
-    __syncthreads();
-    unsigned tk = sh_ticket[0];
-    unsigned prev_t = 0xFFFFFFFFu, prev_g = 0u;
-    for (int it = 1;; ++it) {
-        const bool in_range = tk < G.total;
-        const unsigned g = in_range ? tk / Tf : 0u, t = in_range ? tk - g * Tf : 0u;
-        const unsigned tt = t % (unsigned)G.tpp, kk = t / (unsigned)G.tpp;
-        if (warp == 0) {
-            // publish the previous item (its stores are complete: barrier
-            // below), then lanes 0..4 wait on the 5 dependences in parallel
-            // while lane 5 takes the next ticket
-            if (lane == 0 && prev_t != 0xFFFFFFFFu) {
-                __threadfence();
-                st_release_u32(&done[prev_t], prev_g + 1u);
-            }
-            __syncwarp();
-            unsigned stop = !in_range || ld_volatile_u32(&ctrl[1]) != 0u;
-            const unsigned long long t0 = global_ns();
-            if (!stop && lane < 5) {
-                int dep = -1;
-                unsigned need = g;
-                if (lane == 0) dep = (int)t;
-                if (lane == 1 && tt > 0) dep = (int)t - 1;
-                if (lane == 2 && tt + 1 < (unsigned)G.tpp) dep = (int)t + 1;
-                if (lane == 3 && kk > 0) dep = (int)(t - G.tpp);
-                if (lane == 4 && kk + 1 < (unsigned)L.n3) dep = (int)(t + G.tpp);
-                if (lane > 0) need = g > 0u ? g - 1u : 0u;
-                if (dep >= 0 && need > 0u && !wave_wait(&done[dep], need, ctrl, t0)) stop = 1;
-                if (lane == 0 && test_wait && tk == 0u && !stop &&
-                    !wave_wait(&ctrl[3], 1u, ctrl, t0))
-                    stop = 1;
-            }
-            stop = __any_sync(0xffffffffu, stop) ? 1u : 0u;
-            if (lane == 5 && !stop) sh_ticket[it & 1] = atomicAdd(&ctrl[0], 1u);
-            if (lane == 0) sh_stop = stop;
-        }
-        __syncthreads();
-        if (sh_stop) break;
-        if (warp < 4) {
-            const unsigned s = g % (unsigned)G.Ts;
-            if (g < red_steps && s < (unsigned)L.n4)
-                wave_tile<0, kUnit>(L, G, x, B, Gm, W, omega, (int)tt, (int)kk, (int)s, warp);
-        } else if (g >= 2u) {
-            const unsigned gb = g - 2u, f = gb % (unsigned)G.Ts;
-            if (gb < red_steps && f < (unsigned)L.n4)
-                wave_tile<1, kUnit>(L, G, x, B, Gm, W, omega, (int)tt, (int)kk, (int)f, warp - 4);
-        }
-        __syncthreads();
-        prev_t = t;
-        prev_g = g;
-        tk = sh_ticket[it & 1];
-    }
-}
-
-int wave_tiles(const Layout &L) { return wave_geo(L, 1).Tf; }
-
-int wave_max_ctas_per_sm()
-{
-    int nb = 0, nb2 = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_wave<true>, 32 * kWaveWarps,
-                                                      0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_sweep_wave<false>, 32 * kWaveWarps,
-                                                      0) != cudaSuccess)
-        return 1;
-    nb = std::min(nb, nb2);
-    return nb < 1 ? 1 : nb;
-}
-
-// Launches of at most 2^31 items each.  The caller zeroes ctrl before the
-// first; between launches only the ticket, the abort flag and done[] are
-// cleared, so an error raised by an earlier launch (ctrl[2]) survives to the
-// host's check after the last one.
-void launch_sweep_wave(const Layout &L, int nsweeps, float *x, const float *beta,
-                       const float *gamma, const float *W, float omega, unsigned *ctrl, int ctas,
-                       int test_wait, cudaStream_t st)
-{
-    const WaveGeo one = wave_geo(L, 1);
-    const long long per_sweep = (long long)one.Ts * one.Tf;
-    const int max_sweeps = (int)std::max(1LL, ((1LL << 31) - 2LL * one.Tf) / per_sweep);
-    for (int done_sw = 0; done_sw < nsweeps;) {
-        const int n = std::min(nsweeps - done_sw, max_sweeps);
-        const WaveGeo G = wave_geo(L, n);
-        if (done_sw > 0) {
-            cudaMemsetAsync(ctrl, 0, 2 * sizeof(unsigned), st);
-            cudaMemsetAsync(ctrl + 4, 0, (size_t)G.Tf * sizeof(unsigned), st);
-        }
-        if (gamma)
-            k_sweep_wave<false><<<ctas, 32 * kWaveWarps, 0, st>>>(L, G, x, beta, gamma, W, omega, n,
-                                                                 ctrl, test_wait);
-        else
-            k_sweep_wave<true><<<ctas, 32 * kWaveWarps, 0, st>>>(L, G, x, beta, nullptr, W, omega,
-                                                                n, ctrl, test_wait);
-        done_sw += n;
-    }
-}
-
 // ---------------------------------------------------- symmetric scaling
 
 // The system D u - c sum_f w_f u_nb = b, divided by c row by row, is
