@@ -58,7 +58,8 @@ typedef struct {
 /* Parameters.  seg4d_default_params() fills the values used throughout
  * Section 4 of the paper (delta = vartheta = 0.5, h = 0.01, tau = 0.01,
  * eps = 1, sigma = h^2/8, R = 12, lambda = 0.87) plus the readings for the
- * values the paper does not give (K = 1, v = 1, omega = 1.8, the stopping
+ * values the paper does not give (K = 1, v = 1, omega = 1.6 raised at run time
+ * by omega_adapt, the stopping
  * rule below). */
 typedef struct {
     double h[4];        /* voxel sizes h1..h4 (Eq. new1)                            */
@@ -72,7 +73,8 @@ typedef struct {
     double R_init;      /* radius (voxels) of the initial peak (Eq. initialcond)    */
     double v_init;      /* 1/v is the peak height of u0 (Eq. initialcond)           */
     double sigma_t;     /* presmoothing: one implicit heat step of this length      */
-    double omega;       /* SOR relaxation of the step solves (Eq. 5.33)             */
+    double omega;       /* SOR relaxation of the step solves (Eq. 5.33); with
+                           omega_adapt, the value each solve starts from        */
     double omega_smooth;/* SOR relaxation of the presmoothing solves                */
     double tol;         /* stop when ||b - A u||_2 <= tol ||b||_2 (step solves; see
                            also tol_inf)                                        */
@@ -100,6 +102,12 @@ typedef struct {
                            of the exact solve.  0 disables it; the default is
                            1e-5 (the FP32 floor of max |r| on the measured
                            workloads lies between 2e-6 and 5e-6 of max |b|)  */
+    int omega_adapt;    /* 1: the step solves choose their SOR relaxation at run
+                           time (Young's relation for the consistently ordered
+                           red-black matrix: the contraction observed at omega
+                           gives the Jacobi radius mu and the best relaxation
+                           2 / (1 + sqrt(1 - mu^2))); each solve starts at
+                           omega and only raises it.  0: omega is used as is  */
 } seg4d_params;
 
 /* a segmentation seed: centre c_m (voxel units, 0-based) inside frame `frame` */
@@ -171,7 +179,8 @@ seg4d_status seg4d_destroy(seg4d *h);
 
 /* Copy the parameters.  Errors: INVALID (non-finite or out of range:
  * h, tau, eps > 0; K >= 0; delta, vartheta, lambda in [0,1]; radii > 0;
- * 0 < omega, omega_smooth < 2; tol, tol_smooth > 0; tol_inf >= 0; max_iters >= 1;
+ * 0 < omega, omega_smooth < 2; tol, tol_smooth > 0; tol_inf >= 0; omega_adapt 0 or 1;
+ * max_iters >= 1;
  * check_every >= 1; precision 0). */
 seg4d_status seg4d_set_params(seg4d *h, const seg4d_params *p);
 

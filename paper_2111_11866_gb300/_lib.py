@@ -47,7 +47,7 @@ class CParams(C.Structure):
                 ("omega_smooth", C.c_double), ("tol", C.c_double), ("tol_smooth", C.c_double),
                 ("max_iters", C.c_int), ("check_every", C.c_int), ("precision", C.c_int),
                 ("sweep_variant", C.c_int), ("ctas_per_sm", C.c_int), ("wait_test", C.c_int),
-                ("tol_inf", C.c_double)]
+                ("tol_inf", C.c_double), ("omega_adapt", C.c_int)]
 
 
 class CSeed(C.Structure):
@@ -137,7 +137,7 @@ class Params:
     R_init: float = 12.0
     v_init: float = 1.0
     sigma_t: float = 0.01 ** 2 / 8.0
-    omega: float = 1.8
+    omega: float = 1.6
     omega_smooth: float = 1.0
     tol: float = 1e-5
     tol_smooth: float = 1e-6
@@ -148,6 +148,7 @@ class Params:
     ctas_per_sm: int = 0
     wait_test: int = 0
     tol_inf: float = 1e-5
+    omega_adapt: int = 1
 
     @classmethod
     def defaults(cls) -> "Params":

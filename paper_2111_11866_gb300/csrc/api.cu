@@ -287,8 +287,9 @@ seg4d_status ensure_solve_arrays(seg4d *h, bool mixed)
 // ends a solve whose max |r| has reached its FP32 floor).
 seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol, int max_iters,
                           int check_every, SolveOut &out, bool mixed = false,
-                          double tol_inf = 0.0)
+                          double tol_inf = 0.0, double *omega_adapt = nullptr)
 {
+    if (omega_adapt) omega = *omega_adapt;
     const Layout &L = h->L;
     seg4d_status st = reduce_into(h, 0, brec);   // scal[0..2] = sum b^2, min b, max b
     if (st) return st;
@@ -334,12 +335,21 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
         out.bmax = std::max(std::fabs(h->host_scal[1]), std::fabs(h->host_scal[2]));
         if (!std::isfinite(rn))
             return fail(h, SEG4D_ERR_NOT_CONVERGED, "residual is not finite");
+        const double prev_rn = cs.prev_rn;
+        const int prev_it = cs.prev_it;
         if (check_decision(cs, rn, bn, out.res_inf, out.bmax, it, tol, tol_inf, check_every,
                            mixed, batch) != kGoOn) {
+            if (omega_adapt) *omega_adapt = omega;
             out.converged = true;
             return SEG4D_OK;
         }
-        if (it >= max_iters) return SEG4D_OK;   // not converged; caller reports it
+        if (it >= max_iters) {   // not converged; caller reports it
+            if (omega_adapt) *omega_adapt = omega;
+            return SEG4D_OK;
+        }
+        // relaxation from the contraction of the last batch (sor_omega_update)
+        if (omega_adapt && prev_rn > 0.0 && rn < prev_rn && it - prev_it >= 4)
+            omega = sor_omega_update(omega, std::pow(rn / prev_rn, 1.0 / (it - prev_it)));
         const int n = std::min(batch, max_iters - it);
         CK(cudaEventRecord(h->evs0, h->stream));
         if (mixed) {
@@ -540,8 +550,13 @@ seg4d_status one_solve(seg4d *h, seg4d_info *info, long long &sweeps)
     h->has_coef = true;
     const bool mixed = h->p.precision == 1;
     SolveOut so;
+    // with omega_adapt, every solve starts from params.omega and raises it
+    // from its own residual history (so a step's result does not depend on
+    // earlier steps' solves beyond u itself)
+    double om = h->p.omega;
     seg4d_status st = solve_system(h, h->u, brec, h->p.omega, h->p.tol, h->p.max_iters,
-                                   h->p.check_every, so, mixed, h->p.tol_inf);
+                                   h->p.check_every, so, mixed, h->p.tol_inf,
+                                   h->p.omega_adapt ? &om : nullptr);
     if (st) return st;
     sweeps += so.iters;
     if (info) {
@@ -636,7 +651,8 @@ void seg4d_default_params(seg4d_params *p)
     p->R_init = 12.0;
     p->v_init = 1.0;
     p->sigma_t = 0.01 * 0.01 / 8.0;
-    p->omega = 1.8;
+    p->omega = 1.6;
+    p->omega_adapt = 1;
     p->omega_smooth = 1.0;
     p->tol = 1e-5;
     p->tol_inf = 1e-5;
@@ -787,6 +803,8 @@ seg4d_status seg4d_set_params(seg4d *h, const seg4d_params *p)
         return fail(h, SEG4D_ERR_INVALID, "max_iters and check_every must be >= 1");
     if (p->precision != 0 && p->precision != 1)
         return fail(h, SEG4D_ERR_INVALID, "precision must be 0 or 1");
+    if (p->omega_adapt != 0 && p->omega_adapt != 1)
+        return fail(h, SEG4D_ERR_INVALID, "omega_adapt must be 0 or 1");
     if (p->sweep_variant != 1 || p->ctas_per_sm != 0 || p->wait_test != 0)
         return fail(h, SEG4D_ERR_INVALID,
                     "sweep_variant must be 1, ctas_per_sm and wait_test 0 (reserved)");

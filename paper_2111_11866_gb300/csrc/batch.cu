@@ -348,6 +348,7 @@ enum { kSolveRun = 0, kSolveOk = 1, kSolveFail = 2 };
 struct BSolve {
     double bnorm, bmax;   // ||b||_2 and max |b| of the window's system
     double last_rel;      // ||r||_2 / ||b||_2 at its last test
+    double omega;         // its SOR relaxation (raised by sor_omega_update when adaptive)
     CheckState cs;        // residual history of its tests
     int next_check;       // sweep count of its next test (a multiple of kCheckGrid)
     int state;            // kSolveRun, kSolveOk, kSolveFail
@@ -374,7 +375,7 @@ struct DevTabs {
 // pass left in L2); the per-voxel work is k_bsweep's.
 template <int C, bool kMixed, int N = kMixed ? kVecBF16 : kVecF32>
 __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_bsweep_dev(
-    const BWin *__restrict__ wins, DevTabs T, float omega)
+    const BWin *__restrict__ wins, DevTabs T, const BSolve *__restrict__ sw)
 {
     const int nw = *T.act_n;
     const long long total = nw > 0 ? T.act_pt[nw] : 0;
@@ -382,6 +383,7 @@ __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_bsweep_dev(
         const long long b = C ? total - 1 - g : g;
         const int i = find_win(T.act_pt, nw, b);
         const BWin &wd = wins[T.act_idx[i]];
+        const float omega = (float)sw[T.act_idx[i]].omega;
         const Layout L = wd.L;
         RowPos rp{0, 0, 0, 0};
         int s0 = 0, row = 0;
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(256) k_breduce_dev(DevTabs T, const double *__
 
 struct DecideConst {
     double tol, tol_inf;
-    int check_every, max_iters, mixed, K;
+    int check_every, max_iters, mixed, K, adapt;
 };
 
 // Block-wide exclusive prefix sum (1024 threads at most); *total gets the
@@ -508,6 +510,8 @@ __global__ void __launch_bounds__(1024) k_bdecide(BSolve *__restrict__ sw, int n
             continue;
         }
         int n = P.check_every;
+        const double prev_rn = s.cs.prev_rn;
+        const int prev_it = s.cs.prev_it;
         const int dec = check_decision(s.cs, rn, s.bnorm, rinf, s.bmax, it, P.tol, P.tol_inf,
                                        P.check_every, P.mixed != 0, n);
         if (dec != kGoOn) {
@@ -519,6 +523,8 @@ __global__ void __launch_bounds__(1024) k_bdecide(BSolve *__restrict__ sw, int n
             s.iters = it;
         } else {
             s.next_check = (it + n + P.K - 1) / P.K * P.K;
+            if (P.adapt && prev_rn > 0.0 && rn < prev_rn && it - prev_it >= 4)
+                s.omega = sor_omega_update(s.omega, pow(rn / prev_rn, 1.0 / (it - prev_it)));
         }
     }
     __syncthreads();
@@ -965,7 +971,7 @@ struct SolveItem {
 // windows, so its result is the same alone or in any mix.
 seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double omega, double tol,
                          int max_iters, int check_every, long long &sweeps_total,
-                         bool mixed = false, double tol_inf = 0.0)
+                         bool mixed = false, double tol_inf = 0.0, bool adapt = false)
 {
     const int ns = (int)items.size();
     if (ns == 0) return SEG4D_OK;
@@ -981,7 +987,8 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
         cnt[i] = win_gtiles(ws[i]->L, N);
         cnt[ns + i] = win_tiles(ws[i]->L);
         cnt[2 * ns + i] = chunks_of(*ws[i]);
-        b->h_sw[i] = BSolve{items[i].bnorm, items[i].bmax, 0.0, CheckState{}, 0, kSolveRun, 0, 0};
+        b->h_sw[i] = BSolve{items[i].bnorm, items[i].bmax, 0.0, omega, CheckState{}, 0,
+                            kSolveRun, 0, 0};
         b->h_tab_int[i] = i;   // due_idx
     }
     b->h_tab_int[ns] = ns;    // due_n
@@ -1016,7 +1023,8 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
     BCK(cudaMemcpyAsync(T.due_c, ht + ns + 1, (ns + 1) * sizeof(long long),
                         cudaMemcpyHostToDevice, b->stream));
     BCK(cudaMemsetAsync(T.act_n, 0, sizeof(int), b->stream));
-    const DecideConst P{tol, tol_inf, check_every, max_iters, mixed ? 1 : 0, kCheckGrid};
+    const DecideConst P{tol, tol_inf, check_every, max_iters, mixed ? 1 : 0, kCheckGrid,
+                        adapt ? 1 : 0};
     double *amax = b->d_parts + 3 * b->parts_cap;
     const int sms = b->num_sms;
     const unsigned g_sweep = (unsigned)(sms * (N == 2 ? SEG4D_VEC2_MINB : SEG4D_VEC4_MINB));
@@ -1029,15 +1037,11 @@ seg4d_status batch_solve(seg4d_batch *b, std::vector<SolveItem> &items, double o
             BCK(cudaEventRecord(b->ev_s0[slot], b->stream));
             for (int s = 0; s < kCheckGrid; ++s) {
                 if (mixed) {
-                    k_bsweep_dev<0, true><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T,
-                                                                          (float)omega);
-                    k_bsweep_dev<1, true><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T,
-                                                                          (float)omega);
+                    k_bsweep_dev<0, true><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T, b->d_sw);
+                    k_bsweep_dev<1, true><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T, b->d_sw);
                 } else {
-                    k_bsweep_dev<0, false><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T,
-                                                                           (float)omega);
-                    k_bsweep_dev<1, false><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T,
-                                                                           (float)omega);
+                    k_bsweep_dev<0, false><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T, b->d_sw);
+                    k_bsweep_dev<1, false><<<g_sweep, 256, 0, b->stream>>>(b->d_wins, T, b->d_sw);
                 }
             }
             BCK(cudaEventRecord(b->ev_s1[slot], b->stream));
@@ -1248,7 +1252,7 @@ seg4d_status batch_step(seg4d_batch *b, std::vector<Window *> &act, long long &s
                                            std::fabs(b->h_out[4 * i + 2])),
                                   0, false, false, 0, CheckState{}});
     if ((st = batch_solve(b, items, p.omega, p.tol, p.max_iters, p.check_every, sweeps, mixed,
-                          p.tol_inf)))
+                          p.tol_inf, p.omega_adapt != 0)))
         return st;
     std::vector<Window *> ok;
     for (auto &itm : items) {
@@ -1384,7 +1388,8 @@ seg4d_status seg4d_batch_set_params(seg4d_batch *b, const seg4d_params *p)
         !(p->omega_smooth > 0 && p->omega_smooth < 2) || !(p->tol > 0) || !(p->tol_smooth > 0) ||
         p->max_iters < 1 || p->check_every < 1 || !(p->tau > 0) || !(p->eps > 0) ||
         !(p->sigma_t > 0) || !(p->r_ball > 0) || !(p->R_init > 0) || !(p->v_init > 0) ||
-        !(p->tol_inf >= 0) || !std::isfinite(p->tol_inf))
+        !(p->tol_inf >= 0) || !std::isfinite(p->tol_inf) ||
+        (p->omega_adapt != 0 && p->omega_adapt != 1))
         return bfail(b, SEG4D_ERR_INVALID, "batch_set_params: invalid parameters");
     for (int d = 0; d < 4; ++d)
         if (!(p->h[d] > 0) || !std::isfinite(p->h[d]))

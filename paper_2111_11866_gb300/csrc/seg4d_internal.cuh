@@ -207,6 +207,26 @@ __host__ __device__ inline int next_check_batch(double rn, double prev_rn, int i
     return isfinite(want) ? (int)fmin((double)hi, fmax((double)lo, want)) : check_every;
 }
 
+// Run-time choice of the SOR relaxation (Eq. 5.33 leaves omega open).  The
+// red-black ordering makes the step matrix consistently ordered, so Young's
+// relation ties the spectral radius lam of the SOR iteration at relaxation
+// omega to the Jacobi radius mu: (lam + omega - 1)^2 = lam omega^2 mu^2, and
+// the best relaxation is omega_b = 2 / (1 + sqrt(1 - mu^2)).  Given the
+// residual contraction per sweep lam observed at omega, this returns the
+// estimate of omega_b when lam shows omega below it (lam > omega - 1; at or
+// past omega_b, lam = omega - 1 and there is nothing to learn), never less
+// than omega and at most 1.95.  Host and device use it (single grid and
+// batched windows).
+__host__ __device__ inline double sor_omega_update(double omega, double lam)
+{
+    if (!(lam > 0.0 && lam < 1.0) || lam <= omega - 1.0 + 0.02) return omega;
+    const double a = lam + omega - 1.0;
+    const double mu2 = a * a / (lam * omega * omega);
+    if (!(mu2 < 1.0)) return omega;
+    const double wb = 2.0 / (1.0 + sqrt(1.0 - mu2));
+    return fmin(fmax(wb, omega), 1.95);
+}
+
 // Stopping decision at a check of a solve.  The test has two parts:
 // ||r||_2 <= tol ||b||_2 and, with tol_inf > 0, max |r| <= tol_inf max |b|
 // (a per-voxel bound, ||A^-1||_inf <= 1).  When the 2-norm part holds but the

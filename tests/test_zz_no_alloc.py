@@ -71,7 +71,7 @@ def test_noalloc_matches_allocating_path_twice():
         # and the FP64 oracle's residual of the very same arrays
         r = O.residual(diag.cpu().numpy(), off.cpu().numpy(), b.cpu().numpy(), u.cpu().numpy())
         ro = float(np.sqrt((r * r).sum()))
-        bo = float(np.sqrt((b.cpu().double() ** 2).sum()))
+        bo = float(torch.sqrt((b.double() ** 2).sum()))
         assert abs(rn - ro) <= REL_TOL * ro, (dims, rn, ro)
         assert abs(bn - bo) <= REL_TOL * bo, (dims, bn, bo)
 
