@@ -236,8 +236,8 @@ __host__ __device__ inline double sor_omega_update(double omega, double lam)
 // (about D ulp(u) at a voxel), and the solve stops there (kStopFloor; the
 // achieved max |r| is what the caller reports).  Otherwise `batch` is the
 // number of sweeps to the next check: from the 2-norm history, or, once the
-// 2-norm part holds, from the max |r| history (at least check_every).  Only
-// the solve's own residual history enters.
+// 2-norm part holds, from the max |r| history.  Only the solve's own
+// residual history enters.
 struct CheckState {
     double prev_rn = -1.0, prev_inf = -1.0;
     int prev_it = 0;
@@ -258,9 +258,8 @@ __host__ __device__ inline int check_decision(CheckState &cs, double rn, double 
     }
     if (res == kGoOn) {
         if (l2) {
-            const int n = next_check_batch(rinf, cs.prev_inf, it, cs.prev_it, tol_inf, bmax,
-                                           check_every, mixed);
-            batch = n > check_every ? n : check_every;
+            batch = next_check_batch(rinf, cs.prev_inf, it, cs.prev_it, tol_inf, bmax,
+                                     check_every, mixed);
         } else {
             batch = next_check_batch(rn, cs.prev_rn, it, cs.prev_it, tol, bn, check_every, mixed);
         }
