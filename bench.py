@@ -499,7 +499,7 @@ def run_medium(args, params, local):
     return out
 
 
-def run_paper_scale(nsteps, params, local):
+def run_paper_scale(nsteps, params, local, mixed_steps=0):
     """A grid of the size of the paper's largest stack (567x577x147 x 70
     frames, 3.37G voxels; the paper ran it on six nodes with 1012 GB) on one
     GPU with a lean handle (80 B/voxel): synthetic nuclei made frame by frame
@@ -540,8 +540,25 @@ def run_paper_scale(nsteps, params, local):
         sweeps = info["sweeps_total"]
         peak, peak_kind = _peaks()
         rate = nvox * sweeps / (info["sweep_ms"] / 1000.0)
+        # the same handle continues in mixed precision (BF16 sweep weights,
+        # FP32 defect passes): the weights fit beside the lean grid
+        mixed = None
+        if mixed_steps > 0:
+            seg.set_params(precision=1)
+            e0.record(stream)
+            infm = seg.step(mixed_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msm = e0.elapsed_time(e1)
+            mixed = {"steps": mixed_steps, "value": nvox * infm["sweeps_total"] / (msm / 1000.0),
+                     "unit": "voxel-sweeps/s", "ms_per_time_step": msm / mixed_steps,
+                     "sweeps_per_time_step": infm["sweeps_total"] / mixed_steps,
+                     "sweep_rate": nvox * infm["sweeps_total"] / (infm["sweep_ms"] / 1000.0),
+                     "last_res_rel": infm["res_rel"],
+                     "device_used_gb": (lambda fr: (fr[1] - fr[0]) / 1e9)(
+                         torch.cuda.mem_get_info())}
         return {"workload": f"567x577x147x70 ({nvox} voxels, {count} nuclei), {nsteps} steps, "
-                            f"lean handle", "voxels": nvox,
+                            f"lean handle", "voxels": nvox, "mixed_precision": mixed,
                 "device_gb": _lib.Seg4D.device_bytes(dims, lean=True) / 1e9,
                 "value": nvox * sweeps / (ms / 1000.0), "unit": "voxel-sweeps/s",
                 "ms_per_time_step": ms / nsteps, "sweeps_per_time_step": sweeps / nsteps,
@@ -678,6 +695,8 @@ def main():
                     help="segmentations of the medium workload in mixed precision (0 = skip)")
     ap.add_argument("--paper-steps", type=int, default=5,
                     help="time steps of the 567x577x147x70 grid with a lean handle (0 = skip)")
+    ap.add_argument("--paper-mixed-steps", type=int, default=3,
+                    help="further time steps of that grid in mixed precision (0 = skip)")
     ap.add_argument("--batched-windows", type=int, default=4096,
                     help="per-nucleus windows of the batched measurement (0 = skip)")
     ap.add_argument("--batched-steps", type=int, default=30)
@@ -727,7 +746,7 @@ def main():
     if args.medium_steps > 0:
         medium = run_medium(args, params, local)
     if args.paper_steps > 0:
-        paper = run_paper_scale(args.paper_steps, params, local)
+        paper = run_paper_scale(args.paper_steps, params, local, args.paper_mixed_steps)
     if args.batched_windows > 0:
         batched = run_batched(args.batched_windows, args.batched_steps, params)
     if args.serve_seconds > 0:

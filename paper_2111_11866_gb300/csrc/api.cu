@@ -37,7 +37,7 @@ struct seg4d {
     // colour-split device arrays ([2][S] unless noted)
     float *u = nullptr, *beta = nullptr, *gamma = nullptr, *diag = nullptr;
     float *W = nullptr;            // [8][S] face weights by red end
-    float *G = nullptr;            // [2][8][S] face edge coefficients
+    float *G = nullptr;            // face edge coefficients: [8][S] by red end + side table
     float *I0 = nullptr, *ITH = nullptr, *Is0 = nullptr, *IsTH = nullptr;
     int *owner = nullptr;
     float *stage = nullptr;        // natural-layout staging, n1*n2*n3*n4 floats
@@ -147,14 +147,14 @@ size_t bytes_for(const Layout &L, long long nv, bool lean = false)
     if (lean) {
         // u, beta, gamma, diag, W, G, owner, ib, rho, dlt (see seg4d_create_ex)
         const size_t S = (size_t)L.S;
-        return 2 * S * 4 * 4 + 8 * S * 4 + 16 * S * 4 + 2 * S * 4 + 3 * 2 * S * 4 +
+        return 2 * S * 4 * 4 + 8 * S * 4 + (size_t)g_floats(L) * 4 + 2 * S * 4 + 3 * 2 * S * 4 +
                4 * kPartCap * sizeof(double) + 8 * sizeof(double);
     }
     const size_t S = (size_t)L.S;
     size_t b = 0;
     b += 2 * S * sizeof(float) * 4;        // u, beta, gamma, diag
     b += 8 * S * sizeof(float);            // W
-    b += 16 * S * sizeof(float);           // G
+    b += (size_t)g_floats(L) * sizeof(float);   // G, once per face
     b += 2 * S * sizeof(float) * 4;        // I0, ITH, Is0, IsTH
     b += 2 * S * sizeof(int);              // owner
     b += (size_t)nv * sizeof(float);       // staging
@@ -472,7 +472,7 @@ seg4d_status run_setup(seg4d *h, long long &sweeps)
                         "a lean handle keeps no image after its set-up: call set_image again");
         if ((st = upload_seeds(h))) return st;
         // Where the image fields live.  A lean handle keeps them inside G (not
-        // computed yet; 8 planes of 2S floats): I0 in plane 0, I^TH in plane 2,
+        // computed yet; at least 4 planes of 2S floats): I0 in plane 0, I^TH in plane 2,
         // I_sigma^TH in plane 3, I_sigma^0 in u (set from the seeds at the
         // end); the owner keys borrow W.
         const size_t plane = 2 * (size_t)L.S;
@@ -715,7 +715,7 @@ seg4d_status seg4d_create_ex(const seg4d_dims *dims, void *cuda_stream, int flag
     std::vector<A> allocs = {
         {(void **)&h->u, 2 * S * 4},     {(void **)&h->beta, 2 * S * 4},
         {(void **)&h->gamma, 2 * S * 4}, {(void **)&h->diag, 2 * S * 4},
-        {(void **)&h->W, 8 * S * 4},     {(void **)&h->G, 16 * S * 4},
+        {(void **)&h->W, 8 * S * 4},     {(void **)&h->G, (size_t)g_floats(L) * 4},
         {(void **)&h->owner, 2 * S * 4},
         {(void **)&h->partials, 4 * kPartCap * sizeof(double)},
         {(void **)&h->scal, 8 * sizeof(double)},
@@ -1063,7 +1063,7 @@ seg4d_status seg4d_read_field(seg4d *h, int field, float *dst, size_t n, int on_
         }
     }
     if (field == SEG4D_FIELD_G)
-        launch_faces_natural_from_split(h->L, h->G, nat8, h->stream);
+        launch_G_natural(h->L, h->G, nat8, h->stream);
     else
         launch_off_natural(h->L, h->W, h->gamma, h->diag, nat8, h->stream);
     cudaError_t e = cudaGetLastError();

@@ -163,9 +163,10 @@ __global__ void __launch_bounds__(256, 2) k_bcoef(const BWin *__restrict__ wins,
         for (int C = 0; C < 2; ++C) {
             const bool act = in_win && 2 * s + (C ^ rp.p) < L.n1;
             float g[8];
-#pragma unroll
-            for (int f = 0; f < 8; ++f)
-                g[f] = act ? G[((long long)C * 8 + f) * L.S + q] : 0.0f;
+            if (C)
+                load_G8<1>(L, G, act, row, s, rp, g);
+            else
+                load_G8<0>(L, G, act, row, s, rp, g);
             float u0, sm[4], sp[4], ed[6][2][2];
             if (C)
                 coef_gather<1>(L, u, act, row, s, rp, u0, sm, sp, ed);
@@ -812,7 +813,7 @@ Layout layout_of(const seg4d_dims &d)
 size_t main_bytes(const Layout &L, int nseeds, bool mixed)
 {
     const size_t S = (size_t)L.S;
-    return align_up(32 * S * 4) + align_up(2 * S * 4) +
+    return align_up((16 * S + (size_t)g_floats(L)) * 4) + align_up(2 * S * 4) +
            align_up(sizeof(SeedDev) * std::max(nseeds, 1)) +
            align_up(sizeof(SeedStat) * std::max(nseeds, 1)) + 3 * align_up(2 * S * 4) +
            (mixed ? align_up(8 * S * 2) + align_up(2 * S * 4) : 0);
@@ -834,8 +835,8 @@ void carve(seg4d_batch *b, Window &w)
     w.d.gamma = f + 4 * S;
     w.d.diag = f + 6 * S;
     w.d.W = f + 8 * S;
-    w.d.G = f + 16 * S;
-    char *p = m + align_up(32 * S * 4);
+    w.d.G = f + 16 * S;   // g_floats(L): 8 planes by red end + side table
+    char *p = m + align_up((16 * S + (size_t)g_floats(w.L)) * 4);
     w.d.owner = (int *)p;
     p += align_up(2 * S * 4);
     w.d.seeds = (SeedDev *)p;

@@ -65,6 +65,49 @@ inline int plane_tile(int n2, int n3, int n4, int P)
     return kt;
 }
 
+// Face edge coefficients G are stored once per face, by the face's red end,
+// as W is: G[f][S] for the 8 faces f of every red voxel (faces to the
+// Dirichlet ring included).  A black voxel's faces to the ring have no red
+// end; their G follow the planes in a side table (offsets from G + 8 S):
+//   x: per row, [row][side] (i = 0 and i = n1-1);
+//   y: rows j = 0 and j = n2-1, [side][k + n3 l][slot];
+//   z: rows k = 0 and k = n3-1, [side][j + n2 l][slot];
+//   t: rows l = 0 and l = n4-1, [side][j + n2 k][slot].
+struct GbOff {
+    long long x, y, z, t, total;
+};
+
+__host__ __device__ inline GbOff gb_offsets(const Layout &L)
+{
+    GbOff o;
+    o.x = 0;
+    o.y = 2LL * L.R;
+    o.z = o.y + 2LL * L.n3 * L.n4 * L.P;
+    o.t = o.z + 2LL * L.n2 * L.n4 * L.P;
+    o.total = o.t + 2LL * L.n2 * L.n3 * L.P;
+    return o;
+}
+
+// floats of the G array: the 8 planes and the side table
+__host__ __device__ inline long long g_floats(const Layout &L)
+{
+    return 8LL * L.S + gb_offsets(L).total;
+}
+
+// side-table index of face f (to the ring) of the black voxel in slot s of
+// row `row` at (j, k, l)
+__host__ __device__ inline long long gb_index(const Layout &L, const GbOff &o, int f, int row,
+                                              int s, int j, int k, int l)
+{
+    const int side = f & 1;
+    switch (f >> 1) {
+    case 0: return o.x + 2LL * row + side;
+    case 1: return o.y + ((long long)side * L.n3 * L.n4 + k + (long long)L.n3 * l) * L.P + s;
+    case 2: return o.z + ((long long)side * L.n2 * L.n4 + j + (long long)L.n2 * l) * L.P + s;
+    default: return o.t + ((long long)side * L.n2 * L.n3 + j + (long long)L.n2 * k) * L.P + s;
+    }
+}
+
 // Voxel coordinates -> colour and slot (caller guarantees the voxel exists).
 __host__ __device__ inline long long slot_of(const Layout &L, int i, int j, int k, int l,
                                              int &colour)
@@ -126,8 +169,8 @@ struct Ghost {
 void launch_split_from_natural(const Layout &L, const float *nat, float *split, unsigned *bad,
                                cudaStream_t st);
 void launch_natural_from_split(const Layout &L, const float *split, float *nat, cudaStream_t st);
-void launch_faces_natural_from_split(const Layout &L, const float *split8, float *nat8,
-                                     cudaStream_t st);
+// G ([8][S] planes by red end + side table) -> [voxel][8], x fastest
+void launch_G_natural(const Layout &L, const float *G, float *nat8, cudaStream_t st);
 void launch_owner_natural(const Layout &L, const int *owner, float *nat, cudaStream_t st);
 void launch_off_natural(const Layout &L, const float *W, const float *gamma, const float *diag,
                         float *nat8, cudaStream_t st);

@@ -131,10 +131,34 @@ void launch_natural_from_split(const Layout &L, const float *split, float *nat, 
     k_natural_from_split<<<conv_blocks(L), 256, 0, st>>>(L, split, nat, 1);
 }
 
-void launch_faces_natural_from_split(const Layout &L, const float *split8, float *nat8,
-                                     cudaStream_t st)
+// G per voxel and face in x-fastest order ([voxel][8]) from its per-face
+// storage (load_G8)
+__global__ void k_G_natural(Layout L, const float *__restrict__ G, float *__restrict__ nat8)
 {
-    k_natural_from_split<<<conv_blocks(L), 256, 0, st>>>(L, split8, nat8, 8);
+    const long long n = (long long)L.n1 * L.R;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(v % L.n1);
+        const int row = (int)(v / L.n1);
+        RowPos rp;
+        rp.j = row % L.n2;
+        rp.k = (row / L.n2) % L.n3;
+        rp.l = row / (L.n2 * L.n3);
+        rp.p = (rp.j + rp.k + rp.l) & 1;
+        const int s = i >> 1;
+        float g[8];
+        if (((i + rp.j + rp.k + rp.l) & 1) == 0)
+            load_G8<0>(L, G, true, row, s, rp, g);
+        else
+            load_G8<1>(L, G, true, row, s, rp, g);
+#pragma unroll
+        for (int f = 0; f < 8; ++f) nat8[v * 8 + f] = g[f];
+    }
+}
+
+void launch_G_natural(const Layout &L, const float *G, float *nat8, cudaStream_t st)
+{
+    k_G_natural<<<conv_blocks(L), 256, 0, st>>>(L, G, nat8);
 }
 
 void launch_owner_natural(const Layout &L, const int *owner, float *nat, cudaStream_t st)
@@ -391,8 +415,10 @@ __device__ inline float face_grad_sq_img(const Layout &L, const float *__restric
 }
 
 // G_f = 1 / (1 + K s^2), s = delta |grad^f Is0| + vartheta |grad^f IsTH|,
-// stored [colour][f][slot] for every voxel (both colours: the diagonal of a
-// black voxel needs the G of its faces to the boundary).
+// once per face: every red voxel's 8 faces in the planes, and a black
+// voxel's faces to the Dirichlet ring in the side table (gb_offsets).  The
+// face gradient is symmetric in the face's two cells, so the red end's value
+// is the face's.
 __global__ void k_face_G(Layout L, const float *__restrict__ Is0, const float *__restrict__ IsTH,
                          GConst K, float *__restrict__ G)
 {
@@ -409,11 +435,20 @@ __global__ void k_face_G(Layout L, const float *__restrict__ Is0, const float *_
         const int i = 2 * s + (C ^ ((j + k + l) & 1));
         if (i >= L.n1) continue;
         const int c[4] = {i, j, k, l};
+        const int nn[4] = {L.n1, L.n2, L.n3, L.n4};
+        const GbOff o = gb_offsets(L);
         for (int f = 0; f < 8; ++f) {
+            const int nb = c[f >> 1] + ((f & 1) ? 1 : -1);
+            const bool ring = nb < 0 || nb >= nn[f >> 1];
+            if (C == 1 && !ring) continue;   // stored by the red end
             const float a0 = sqrtf(face_grad_sq_img(L, Is0, c, f, K.inv_h));
             const float a1 = sqrtf(face_grad_sq_img(L, IsTH, c, f, K.inv_h));
             const float sv = K.delta * a0 + K.vartheta * a1;
-            G[((long long)C * 8 + f) * L.S + q] = 1.0f / (1.0f + K.K * sv * sv);
+            const float g = 1.0f / (1.0f + K.K * sv * sv);
+            if (C == 0)
+                G[(long long)f * L.S + q] = g;
+            else
+                G[8 * L.S + gb_index(L, o, f, row, s, j, k, l)] = g;
         }
     }
 }

@@ -141,6 +141,40 @@ __device__ __forceinline__ void decode_item(const ItemDecode &D, const Layout &L
     rp.p = (rp.j + rp.k + rp.l) & 1;
 }
 
+// The 8 face edge coefficients of the voxel in slot s of colour C in row
+// `row` (layout: gb_offsets).  A red voxel reads its own slot of the 8
+// planes; a black voxel reads each interior face across the face (the
+// opposite face of the red neighbour: x-neighbours in red slots s - p and
+// s + 1 - p, y/z/t neighbours in the same slot of rows -+1, -+n2, -+n2 n3)
+// and each face to the ring from the side table.  Zeros when !act.
+template <int C>
+__device__ __forceinline__ void load_G8(const Layout &L, const float *__restrict__ G, bool act,
+                                        int row, int s, const RowPos &rp, float (&g)[8])
+{
+    const long long S = L.S;
+    const long long q = (long long)row * L.P + s;
+    if (C == 0) {
+#pragma unroll
+        for (int f = 0; f < 8; ++f) g[f] = act ? G[(long long)f * S + q] : 0.0f;
+        return;
+    }
+    const int i = 2 * s + 1 - rp.p;
+    const long long dy = L.P, dz = (long long)L.n2 * L.P, dt = (long long)L.n2 * L.n3 * L.P;
+    const long long rb = (long long)row * L.P;
+    const long long idx[8] = {1 * S + rb + s - rp.p, 0 * S + rb + s + 1 - rp.p,
+                              3 * S + q - dy,         2 * S + q + dy,
+                              5 * S + q - dz,         4 * S + q + dz,
+                              7 * S + q - dt,         6 * S + q + dt};
+    const bool in[8] = {i >= 1, i + 1 < L.n1, rp.j > 0, rp.j + 1 < L.n2,
+                        rp.k > 0, rp.k + 1 < L.n3, rp.l > 0, rp.l + 1 < L.n4};
+    const GbOff o = gb_offsets(L);
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+        g[f] = !act ? 0.0f
+                    : (in[f] ? G[idx[f]]
+                             : G[8 * S + gb_index(L, o, f, row, s, rp.j, rp.k, rp.l)]);
+}
+
 // face weight load: FP32, or BF16 widened to FP32
 __device__ __forceinline__ float ldw(const float *p) { return *p; }
 __device__ __forceinline__ float ldw(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
