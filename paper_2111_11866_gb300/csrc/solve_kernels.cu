@@ -155,80 +155,14 @@ void launch_reduce_partials(const double *partials, int nparts, double *out, cud
 // itself in beta (u, plus the Dirichlet column of ghost data when given).  Records: (sum b^2, min b, max b).  Work
 // item t = 2 * tile + colour, tile = 32 slots x 8 rows at one (k, l), one
 // voxel per lane (coef_gather); blocks stride over the items.
-// Coefficients of a black voxel of an interior row (no face on the y, z or t
-// ring) from what the red pass wrote: every interior face f carries
-// w_f = G_f / (A_f h_d^2) at its red end, so A_f = G_f / (w_f h_d^2) and
-// Abar = sqrt(eps^2 + (1/8) sum_f |grad^f u|^2) = sqrt((1/8) sum_f A_f^2):
-// each face gradient is computed once, by its red end.  A face to the x ring
-// (i = 0 or n1 - 1) has no red end; its gradient with the zero ghost value is
-// formed here: normal u0 / h_1, tangential (u(+e_t) - u(-e_t)) / (4 h_t) from
-// the voxel's y, z and t neighbours (the ghost-side diamond points are zero).
-__device__ __forceinline__ void coef_black_derived(const Layout &L, const StepConst &K,
-                                                   const float *__restrict__ u,
-                                                   const float *__restrict__ W,
-                                                   const float (&g)[8], int row, int s,
-                                                   const RowPos &rp, float u0, float &D,
-                                                   float &gm)
-{
-    const long long S = L.S;
-    const long long q = (long long)row * L.P + s;
-    const int i = 2 * s + 1 - rp.p;
-    const long long dy = L.P, dz = (long long)L.n2 * L.P, dt = (long long)L.n2 * L.n3 * L.P;
-    const long long rb = (long long)row * L.P;
-    const long long idx[8] = {1 * S + rb + s - rp.p, 0 * S + rb + s + 1 - rp.p,
-                              3 * S + q - dy,         2 * S + q + dy,
-                              5 * S + q - dz,         4 * S + q + dz,
-                              7 * S + q - dt,         6 * S + q + dt};
-    const bool xin[2] = {i >= 1, i + 1 < L.n1};
-    float A2[8], w[8];
-#pragma unroll
-    for (int f = 0; f < 8; ++f) {
-        if (f < 2 && !xin[f]) continue;
-        w[f] = W[idx[f]];
-        const float A = __fdiv_rn(__fmul_rn(g[f], K.inv_h2[f >> 1]), w[f]);
-        A2[f] = __fmul_rn(A, A);
-    }
-    if (!(xin[0] && xin[1])) {
-        // faces to the x ring (one, or both when n1 = 1): zero ghost value,
-        // the same gradient on either side
-        const float *ur = u;   // red half: the y, z, t neighbours of a black voxel
-        const float nrm = u0 * K.inv_h[0];
-        float g2 = nrm * nrm;
-        const long long off[3] = {dy, dz, dt};
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const float c = 0.25f * (ur[q + off[t]] - ur[q - off[t]]) * K.inv_h[t + 1];
-            g2 += c * c;
-        }
-#pragma unroll
-        for (int f = 0; f < 2; ++f) {
-            if (xin[f]) continue;
-            A2[f] = K.eps2 + g2;
-            w[f] = g[f] * __frsqrt_rn(A2[f]) * K.inv_h2[0];
-        }
-    }
-    float sum = 0.0f, wsum = 0.0f;
-#pragma unroll
-    for (int f = 0; f < 8; ++f) {
-        sum += A2[f];
-        wsum += w[f];
-    }
-    const float Abar = sqrtf(0.125f * sum);
-    const float cc = K.tau * Abar;
-    D = 1.0f + cc * wsum;
-    gm = cc * __frcp_rn(D);
-}
-
 // Coefficients of the step system (coef_finish, Eq. new1) from
-// u = u^{resc,n-1}, in two launches: kC = 0 the red voxels (8 face gradients
-// each, w stored by red end), then kC = 1 the black ones, which take their
-// interior faces from the red pass (coef_black_derived) unless their row
-// touches the y, z or t ring or Dirichlet data are set (then the full
-// gather).  Writes D, gamma = c/D, and b itself in beta (u, plus the
-// Dirichlet column of ghost data when given).  Records: (sum b^2, min b,
-// max b).  Work item t = 2 * tile + kC, tile = 32 slots x 8 rows at one
-// (k, l), one voxel per lane (coef_gather); blocks stride over the items.
-template <bool kGhost, int kC>
+// u = u^{resc,n-1}: w (red voxels store their 8), D, gamma = c/D, and b
+// itself in beta (u, plus the Dirichlet column of ghost data when given).
+// Records: (sum b^2, min b, max b).  Work item t = 2 * tile + colour, tile =
+// 32 slots x 8 rows at one (k, l), one voxel per lane (coef_gather); blocks
+// stride over the items, so a tile's red and black voxels are handled one
+// after the other and the black ones find the shared rows in cache.
+template <bool kGhost>
 __global__ void __launch_bounds__(256, 2) k_step_coef(Layout L, const float *__restrict__ u,
                                                       const float *__restrict__ G, StepConst K,
                                                       float *__restrict__ beta,
@@ -239,61 +173,56 @@ __global__ void __launch_bounds__(256, 2) k_step_coef(Layout L, const float *__r
                                                       ItemDecode dec, unsigned items, Ghost gh)
 {
     Rec3f a = rec3f_init();
-    for (unsigned tt = blockIdx.x; 2 * tt < items; tt += gridDim.x) {
-        const unsigned t = 2 * tt + kC;
+    for (unsigned t = blockIdx.x; t < items; t += gridDim.x) {
         int C, chunk;
         RowPos rp;
         decode_item(dec, L, t, (int)(threadIdx.x >> 5), C, chunk, rp);
         if (rp.j >= L.n2) continue;   // the whole warp
         const int s = chunk * 32 + (int)(threadIdx.x & 31);
-        const bool act = s < L.P && 2 * s + (kC ^ rp.p) < L.n1;
+        const bool act = s < L.P && 2 * s + (C ^ rp.p) < L.n1;
         const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
         const long long q = (long long)row * L.P + s;
         float g[8];
-        load_G8<kC>(L, G, act, row, s, rp, g);
-        const bool row_in = rp.j > 0 && rp.j + 1 < L.n2 && rp.k > 0 && rp.k + 1 < L.n3 &&
-                            rp.l > 0 && rp.l + 1 < L.n4;   // uniform over the warp
-        float D, gm, b;
-        if (kC == 1 && !kGhost && row_in) {
-            if (!act) continue;
-            b = u[L.S + q];
-            coef_black_derived(L, K, u, W, g, row, s, rp, b, D, gm);
-        } else {
-            float u0, sm[4], sp[4], ed[6][2][2];
-            coef_gather<kC>(L, u, act, row, s, rp, u0, sm, sp, ed);
-            if (!act) continue;
-            const int i = 2 * s + (kC ^ rp.p);
-            if (kGhost) apply_ghosts(gh, L, i, rp.j, rp.k, rp.l, sm, sp, ed);
-            float w[8], bt, cc;
-            coef_finish(K, g, u0, sm, sp, ed, w, D, bt, gm, cc);
-            // b = u^{n-1}; with Dirichlet data, + c w_f g_f for every face to
-            // the ghost ring (the ghost value's column moved to the right side)
-            b = u0;
-            if (kGhost) {
-                const int c[4] = {i, rp.j, rp.k, rp.l};
-                const int nn[4] = {L.n1, L.n2, L.n3, L.n4};
-                float fold = 0.0f;
+        if (C)
+            load_G8<1>(L, G, act, row, s, rp, g);
+        else
+            load_G8<0>(L, G, act, row, s, rp, g);
+        float u0, sm[4], sp[4], ed[6][2][2];
+        if (C)
+            coef_gather<1>(L, u, act, row, s, rp, u0, sm, sp, ed);
+        else
+            coef_gather<0>(L, u, act, row, s, rp, u0, sm, sp, ed);
+        if (!act) continue;
+        const int i = 2 * s + (C ^ rp.p);
+        if (kGhost) apply_ghosts(gh, L, i, rp.j, rp.k, rp.l, sm, sp, ed);
+        float w[8], D, bt, gm, cc;
+        coef_finish(K, g, u0, sm, sp, ed, w, D, bt, gm, cc);
+        // b = u^{n-1}; with Dirichlet data, + c w_f g_f for every face to the
+        // ghost ring (the ghost value's column moved to the right-hand side)
+        float b = u0;
+        if (kGhost) {
+            const int c[4] = {i, rp.j, rp.k, rp.l};
+            const int nn[4] = {L.n1, L.n2, L.n3, L.n4};
+            float fold = 0.0f;
 #pragma unroll
-                for (int f = 0; f < 8; ++f) {
-                    int e[4] = {c[0], c[1], c[2], c[3]};
-                    e[f >> 1] += (f & 1) ? 1 : -1;
-                    if (e[f >> 1] < 0 || e[f >> 1] >= nn[f >> 1])
-                        fold = __fmaf_rn(w[f], ghost_at(gh, gh.now, L, e[0], e[1], e[2], e[3]),
-                                         fold);
-                }
-                b = __fmaf_rn(cc, fold, u0);
+            for (int f = 0; f < 8; ++f) {
+                int e[4] = {c[0], c[1], c[2], c[3]};
+                e[f >> 1] += (f & 1) ? 1 : -1;
+                if (e[f >> 1] < 0 || e[f >> 1] >= nn[f >> 1])
+                    fold = __fmaf_rn(w[f], ghost_at(gh, gh.now, L, e[0], e[1], e[2], e[3]), fold);
             }
-            if (kC == 0)
-#pragma unroll
-                for (int f = 0; f < 8; ++f) W[(long long)f * L.S + q] = w[f];
+            b = __fmaf_rn(cc, fold, u0);
         }
-        const long long qc = (long long)kC * L.S + q;
+        const long long qc = (long long)C * L.S + q;
+        if (C == 0)
+#pragma unroll
+            for (int f = 0; f < 8; ++f) W[(long long)f * L.S + q] = w[f];
         diag[qc] = D;
         beta[qc] = b;
         gamma[qc] = gm;
         rec3f_add(a, __fmul_rn(b, b), b);
     }
-    block_write3(rec3f_acc(a), partials + 3 * (blockIdx.x + kC * gridDim.x));
+    block_write3(rec3f_acc(a), partials + 3 * blockIdx.x);
 }
 
 int launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,
@@ -308,23 +237,16 @@ int launch_step_coef(const Layout &L, const float *u, const float *G, const doub
     K.tau = (float)tau;
     K.eps2 = (float)(eps * eps);
     const long long items = item_count(L, L.nchunk);
-    // two launches (red, then black) of at most kResBlocks / 2 blocks each:
-    // the records of both fit the scratch array
-    const long long half = items / 2;
-    const int blocks = (int)(half < kResBlocks / 2 ? half : kResBlocks / 2);
-    const ItemDecode dec = make_item_decode(L, L.nchunk);
-    if (ghost) {
-        k_step_coef<true, 0><<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials,
-                                                     dec, (unsigned)items, *ghost);
-        k_step_coef<true, 1><<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials,
-                                                     dec, (unsigned)items, *ghost);
-    } else {
-        k_step_coef<false, 0><<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials,
-                                                      dec, (unsigned)items, Ghost{});
-        k_step_coef<false, 1><<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials,
-                                                      dec, (unsigned)items, Ghost{});
-    }
-    return 2 * blocks;
+    const int blocks = (int)(items < kResBlocks ? items : kResBlocks);
+    if (ghost)
+        k_step_coef<true><<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials,
+                                                  make_item_decode(L, L.nchunk), (unsigned)items,
+                                                  *ghost);
+    else
+        k_step_coef<false><<<blocks, 256, 0, st>>>(L, u, G, K, beta, gamma, diag, W, partials,
+                                                   make_item_decode(L, L.nchunk),
+                                                   (unsigned)items, Ghost{});
+    return blocks;
 }
 
 }  // namespace seg4d_impl
