@@ -292,9 +292,11 @@ seg4d_status seg4d_residual_norms_noalloc(const seg4d_dims *dims, const float *u
  * nucleus, the windows of Section 4's third and fourth experiments) advanced
  * together: every hot kernel launch covers all active windows.  Each window
  * runs exactly the scheme above -- set-up, then per step coefficients, red-
- * black SOR to its own stopping rule, local rescale -- with checks of the
- * stopping rule every check_every sweeps (no adaptive spacing), so its
- * iterates do not depend on which other windows share the batch.
+ * black SOR to its own stopping rule, local rescale.  The solves run in
+ * rounds of 4 sweeps.  Each window's checks, its check spacing (rounded up to
+ * whole rounds) and its run-time SOR relaxation are decided on the device
+ * from its own residuals, so its iterates do not depend on which other
+ * windows share the batch.  max_iters is honoured to the round.
  * ------------------------------------------------------------------------ */
 
 typedef struct seg4d_batch seg4d_batch;
