@@ -161,9 +161,9 @@ void seg4d_default_params(seg4d_params *p);
  * Errors: INVALID (sizes), OOM, CUDA. */
 seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out);
 
-/* seg4d_create with flags.  SEG4D_CREATE_LEAN: 80 instead of 120 bytes per
- * voxel, for the largest grids (the paper's 567x577x147x70 zebrafish stack,
- * Section 4, needs 269 GB this way).  The image fields are kept inside the
+/* seg4d_create with flags.  SEG4D_CREATE_LEAN: 64 instead of about 104 bytes
+ * per voxel, for the largest grids (the paper's 567x577x147x70 zebrafish
+ * stack, Section 4, needs 216 GB this way, 258 GB in mixed precision).  The image fields are kept inside the
  * G array until the set-up has used them (they cannot be read back after
  * it, and new seeds need set_image again; u serves as scratch during the
  * set-up, which therefore re-initialises it from the seeds); the FP32 solve

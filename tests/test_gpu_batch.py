@@ -140,3 +140,35 @@ def test_batch_device_input_and_errors():
         np.testing.assert_array_equal(out.cpu().numpy(), b.read_u(wid))
         with pytest.raises(_lib.Seg4DError):
             b.poll(12345)
+
+
+def test_failed_window_is_reported_and_the_others_go_on():
+    """A window whose residual is not finite (a NaN in its image) fails on the
+    device's decision; the batch stays usable and every other window gets
+    the result it gets alone."""
+    p = _params()
+    specs = {k: _window(*k_n) for k, k_n in enumerate(WINDOWS[:2])}
+    bad = specs[1][0].copy()
+    bad[1, 3, 4, 5] = np.nan
+    mix = {0: specs[0], 1: (bad, specs[1][1], specs[1][2])}
+    with _lib.Batch(1 << 30, 8, params=p) as b:
+        ids = {k: b.add(*v) for k, v in mix.items()}
+        for _ in range(3):
+            b.advance()
+        assert b.poll(ids[1])["state"] == "failed"
+        assert b.poll(ids[0])["state"] == "done"
+        u0 = b.read_u(ids[0])
+    alone = _run_batch({0: specs[0]}, p)
+    np.testing.assert_array_equal(u0, alone[0][0])
+
+
+def test_max_iters_reached_fails_every_window():
+    p = _params()
+    p.max_iters = 4
+    specs = {k: _window(*k_n) for k, k_n in enumerate(WINDOWS[:2])}
+    with _lib.Batch(1 << 30, 8, params=p) as b:
+        ids = {k: b.add(*v) for k, v in specs.items()}
+        b.advance()
+        b.advance()
+        for wid in ids.values():
+            assert b.poll(wid)["state"] == "failed"

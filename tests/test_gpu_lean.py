@@ -1,4 +1,4 @@
-"""A lean handle (SEG4D_CREATE_LEAN, 80 B/voxel): the image fields live inside
+"""A lean handle (SEG4D_CREATE_LEAN, 64 B/voxel): the image fields live inside
 G during the set-up and the FP32 solve sweeps its correction system unscaled.
 The result meets the same parity bar against the oracle; the image fields are
 not kept, and new seeds need the image again."""
@@ -71,3 +71,18 @@ def test_lean_keeps_no_image_and_needs_it_for_new_seeds():
         s.set_image(c.image)
         info = s.step(1)
         assert info["status"] == _lib.OK
+
+
+def test_lean_mixed_precision_matches_oracle():
+    """Mixed precision on a lean handle (the configuration of the paper-scale
+    grid in mixed precision): BF16 sweep weights beside the lean arrays, the
+    same parity bar against the oracle."""
+    c = synth.small_nuclei(seed=77, n=(45, 30, 16, 6), count=3, nsteps=3)
+    p = _lib.Params.defaults()
+    p.r_ball = p.R_init = 6.0
+    p.precision = 1
+    u, _, info = _run(c, p, True, c.nsteps)
+    ref, _ = O.segment(c.image.astype(np.float64), c.seeds, oracle_params(p), nsteps=c.nsteps)
+    assert np.abs(u - ref).max() <= REL_TOL * np.abs(ref).max()
+    assert label_mismatch_outside_band(u, ref) == 0
+    assert info["status"] == _lib.OK
