@@ -85,3 +85,29 @@ def test_medium_two_norm_rule_alone(medium):
     assert gpu["info"]["status"] == _lib.OK
     rel = _check(gpu["u"], r)
     print(f"2-norm rule alone: max|du|/max|u| = {rel:.3e}")
+
+
+def test_large_grid_rows_end_to_end():
+    """The large grid's launch configuration end to end: 512x512 rows (256
+    slots per colour, eight 32-slot chunks) and the tiled plane order of the
+    large grid (kt = 5 z-planes per tile, a ragged last tile), on a
+    512x512x32 x 4-frame crop of its generator (33.5M voxels), 3 steps,
+    against the oracle solved to 1e-12."""
+    try:
+        O.lib(omp=True)
+    except OSError as e:
+        pytest.skip(f"oracle OpenMP build unavailable: {e}")
+    img_d, seeds, _, _ = synth.large("cuda", frames=4, depth=32)
+    img = img_d.cpu().numpy()
+    del img_d
+    p = _lib.Params.defaults()
+    gpu = gpu_run(img, seeds, NSTEPS, p)
+    info = gpu["info"]
+    assert info["status"] == _lib.OK and info["res_inf"] <= p.tol_inf * info["bmax"], info
+    ref, rinfo = O.segment(img.astype(np.float64), seeds, oracle_params(p), nsteps=NSTEPS,
+                           omp=True)
+    assert rinfo["status"] == O.OR_OK
+    err = float(np.abs(gpu["u"] - ref).max())
+    assert err <= REL_TOL * float(np.abs(ref).max()), err
+    assert label_mismatch_outside_band(gpu["u"], ref) == 0
+    assert (ref >= 0.5).sum() > 1000
