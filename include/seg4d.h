@@ -90,8 +90,13 @@ typedef struct {
                            pass r = b - A u; the sweeps solve A_b delta = r and
                            u += delta, so the fixed point is the FP32 system's.
                            Presmoothing solves are always FP32.                    */
-    int sweep_variant;  /* 1: one launch per colour of each red-black sweep (the
-                           only sweep kept; other values are rejected)           */
+    int sweep_variant;  /* one launch per colour of each red-black sweep.  1
+                           (default): the FP32 solve also keeps its scaled face
+                           weights by black end (16 B/voxel more), so the black
+                           pass reads them at its own slots as the red pass
+                           does; 2: the black pass reads them across the faces
+                           (less memory).  Both give identical bits; the lean
+                           handle always works as 2                           */
     int ctas_per_sm;    /* reserved, must be 0                                   */
     int wait_test;      /* reserved, must be 0                                   */
     double tol_inf;     /* per-voxel part of the stopping test of the step solves:
@@ -161,7 +166,7 @@ void seg4d_default_params(seg4d_params *p);
  * Errors: INVALID (sizes), OOM, CUDA. */
 seg4d_status seg4d_create(const seg4d_dims *dims, void *cuda_stream, seg4d **out);
 
-/* seg4d_create with flags.  SEG4D_CREATE_LEAN: 64 instead of about 104 bytes
+/* seg4d_create with flags.  SEG4D_CREATE_LEAN: 64 instead of about 120 bytes
  * per voxel, for the largest grids (the paper's 567x577x147x70 zebrafish
  * stack, Section 4, needs 216 GB this way, 258 GB in mixed precision).  The image fields are kept inside the
  * G array until the set-up has used them (they cannot be read back after

@@ -53,6 +53,7 @@ struct seg4d {
     float *rho = nullptr, *dlt = nullptr; // right-hand side and correction of the correction system
     // FP32 solves (allocated at the first one): scaled weights, r = sqrt(gamma)
     float *Ws = nullptr;           // [8][S] by red end
+    float *Wsb = nullptr;          // [8][S] the same by black end (sweep_variant 1)
     float *rs = nullptr;           // [2][S]
     // Dirichlet data on the ghost ring (seg4d_set_dirichlet); zero when unset
     float *gh_prev = nullptr, *gh_now = nullptr;
@@ -159,7 +160,8 @@ size_t bytes_for(const Layout &L, long long nv, bool lean = false)
     b += 2 * S * sizeof(int);              // owner
     b += (size_t)nv * sizeof(float);       // staging
     b += 4 * kPartCap * sizeof(double) + 8 * sizeof(double);
-    b += 8 * S * sizeof(float) + 2 * S * sizeof(float) * 4;   // FP32 solve: Ws, rs, ib, rho, dlt
+    // FP32 solve: Ws and its copy by black end, rs, ib, rho, dlt
+    b += 2 * 8 * S * sizeof(float) + 2 * S * sizeof(float) * 4;
     return b;
 }
 
@@ -194,6 +196,7 @@ void free_all(seg4d *h)
     cudaFree(h->rho);
     cudaFree(h->dlt);
     cudaFree(h->Ws);
+    cudaFree(h->Wsb);
     cudaFree(h->rs);
     cudaFree(h->gh_prev);
     cudaFree(h->gh_now);
@@ -265,7 +268,8 @@ seg4d_status ensure_solve_arrays(seg4d *h, bool mixed)
              alloc((void **)&h->gb, S2 * sizeof(float));
     if (ok && !mixed && !h->lean)
         ok = alloc((void **)&h->Ws, 4 * S2 * sizeof(float)) &&
-             alloc((void **)&h->rs, S2 * sizeof(float));
+             alloc((void **)&h->rs, S2 * sizeof(float)) &&
+             (h->p.sweep_variant != 1 || alloc((void **)&h->Wsb, 4 * S2 * sizeof(float)));
     if (!ok) return fail(h, SEG4D_ERR_OOM, "solve arrays: device allocation failed");
     return SEG4D_OK;
 }
@@ -302,7 +306,8 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
         h->launches += 1;
     } else {
         launch_plain_prepare(L, h->gamma, h->diag, h->rs, h->ib, h->stream);
-        launch_scaled_weights(L, h->W, h->Ws, h->gamma, h->stream);
+        launch_scaled_weights(L, h->W, h->Ws, h->p.sweep_variant == 1 ? h->Wsb : nullptr,
+                              h->gamma, h->stream);
         h->launches += 2;
     }
     CK_LAUNCH("solve_prepare");
@@ -362,9 +367,11 @@ seg4d_status solve_system(seg4d *h, float *x, int brec, double omega, double tol
         } else {
             const float *gam = h->lean ? h->gamma : nullptr;
             const float *wts = h->lean ? h->W : h->Ws;
+            // the black pass reads the copy by black end at its own slots
+            const float *wblk = !h->lean && h->p.sweep_variant == 1 ? h->Wsb : nullptr;
             for (int s = 0; s < n; ++s) {
                 launch_sweep(L, 0, h->dlt, h->rho, gam, wts, (float)omega, h->stream);
-                launch_sweep(L, 1, h->dlt, h->rho, gam, wts, (float)omega, h->stream);
+                launch_sweep(L, 1, h->dlt, h->rho, gam, wts, (float)omega, h->stream, wblk);
             }
             h->launches += 2LL * n;
             h->sweep_launches += 2LL * n;
@@ -805,9 +812,10 @@ seg4d_status seg4d_set_params(seg4d *h, const seg4d_params *p)
         return fail(h, SEG4D_ERR_INVALID, "precision must be 0 or 1");
     if (p->omega_adapt != 0 && p->omega_adapt != 1)
         return fail(h, SEG4D_ERR_INVALID, "omega_adapt must be 0 or 1");
-    if (p->sweep_variant != 1 || p->ctas_per_sm != 0 || p->wait_test != 0)
+    if ((p->sweep_variant != 1 && p->sweep_variant != 2) || p->ctas_per_sm != 0 ||
+        p->wait_test != 0)
         return fail(h, SEG4D_ERR_INVALID,
-                    "sweep_variant must be 1, ctas_per_sm and wait_test 0 (reserved)");
+                    "sweep_variant must be 1 or 2, ctas_per_sm and wait_test 0 (reserved)");
     const bool geom = std::memcmp(p->h, h->p.h, sizeof(p->h)) != 0 || p->K != h->p.K ||
                       p->delta != h->p.delta || p->vartheta != h->p.vartheta ||
                       p->lambda_th != h->p.lambda_th || p->r_ball != h->p.r_ball ||

@@ -197,9 +197,10 @@ void launch_smooth_coef(const Layout &L, const float *I, const double *h, double
 int launch_step_coef(const Layout &L, const float *u, const float *G, const double *h,
                      double tau, double eps, float *beta, float *gamma, float *diag, float *W,
                      double *partials, const Ghost *ghost, cudaStream_t st);
-// gamma = NULL: a unit-diagonal (scaled) system, G = 1
+// gamma = NULL: a unit-diagonal (scaled) system, G = 1; Wblack (nullable): the
+// weights by black end, read by the black pass at its own slots
 void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,
-                  const float *W, float omega, cudaStream_t st);
+                  const float *W, float omega, cudaStream_t st, const float *Wblack = nullptr);
 // mixed precision (mixed_kernels.cu); Wb is a __nv_bfloat16 [8][S] array
 void launch_mixed_prepare(const Layout &L, const float *W, const float *gamma, const float *diag,
                           void *Wb, float *gb, float *ib, cudaStream_t st);
@@ -214,8 +215,9 @@ void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *
 void launch_apply(const Layout &L, float *u, const float *delta, cudaStream_t st);
 // FP32 solves (see k_scaled_weights): scaled correction weights, per-voxel
 // r = sqrt(gamma) and 1 / (D r); and u <- u + r delta
-void launch_scaled_weights(const Layout &L, const float *W, float *Ws, const float *gamma,
-                           cudaStream_t st);
+// Wsb (nullable): also write the weights by black end
+void launch_scaled_weights(const Layout &L, const float *W, float *Ws, float *Wsb,
+                           const float *gamma, cudaStream_t st);
 void launch_plain_prepare(const Layout &L, const float *gamma, const float *diag, float *rs,
                           float *ib, cudaStream_t st);
 void launch_apply_scaled(const Layout &L, float *u, const float *delta, const float *rs,

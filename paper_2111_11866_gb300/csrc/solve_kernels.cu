@@ -21,8 +21,10 @@ namespace seg4d_impl {
 // ntile n4): the (k, l) planes in the tiled traversal order of Layout::kt.
 // The black pass walks that order backwards, so it starts on the data the
 // red pass touched last, which is still in L2.  The same kernel with BF16 weights
-// sweeps the correction system of the mixed-precision solve.
-template <int C, typename WT, int N, bool kUnit>
+// sweeps the correction system of the mixed-precision solve.  kOwnW: the black
+// pass reads a copy of the weights stored by black end at its own slots, as
+// the red pass reads its own (the same values and bits).
+template <int C, typename WT, int N, bool kUnit, bool kOwnW = false>
 __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_sweep_vec(
     Layout L, FastDiv fn4, float *__restrict__ x, const float *__restrict__ B,
     const float *__restrict__ Gm, const WT *__restrict__ W, float omega)
@@ -43,12 +45,12 @@ __global__ void __launch_bounds__(256, vec_min_blocks<N>()) k_sweep_vec(
     const int s0 = chunk * 32 * N + N * threadIdx.x;
     const bool act = s0 < L.P && 2 * s0 + (C ^ rp.p) < L.n1;
     const int row = rp.j + L.n2 * (rp.k + L.n3 * rp.l);
-    relax_vec<C, WT, N, kUnit>(L, x, B, Gm, W, omega, act, row, s0, rp);
+    relax_vec<C, WT, N, kUnit, kOwnW>(L, x, B, Gm, W, omega, act, row, s0, rp);
 }
 
 template <typename WT, int N, bool kUnit>
 void launch_vec(const Layout &L, int colour, float *x, const float *B, const float *Gm,
-                const WT *W, float omega, cudaStream_t st)
+                const WT *W, float omega, cudaStream_t st, const WT *Wblack = nullptr)
 {
     dim3 block(32, 8);
     dim3 grid((unsigned)(((L.P + 32 * N - 1) / (32 * N)) * L.njb), (unsigned)L.kt,
@@ -56,17 +58,20 @@ void launch_vec(const Layout &L, int colour, float *x, const float *B, const flo
     const FastDiv fn4 = make_fastdiv((unsigned)L.n4);
     if (colour == 0)
         k_sweep_vec<0, WT, N, kUnit><<<grid, block, 0, st>>>(L, fn4, x, B, Gm, W, omega);
+    else if (Wblack)
+        k_sweep_vec<1, WT, N, kUnit, true><<<grid, block, 0, st>>>(L, fn4, x, B, Gm, Wblack,
+                                                                   omega);
     else
         k_sweep_vec<1, WT, N, kUnit><<<grid, block, 0, st>>>(L, fn4, x, B, Gm, W, omega);
 }
 
 void launch_sweep(const Layout &L, int colour, float *x, const float *beta, const float *gamma,
-                  const float *W, float omega, cudaStream_t st)
+                  const float *W, float omega, cudaStream_t st, const float *Wblack)
 {
     if (gamma)
-        launch_vec<float, kVecF32, false>(L, colour, x, beta, gamma, W, omega, st);
+        launch_vec<float, kVecF32, false>(L, colour, x, beta, gamma, W, omega, st, Wblack);
     else
-        launch_vec<float, kVecF32, true>(L, colour, x, beta, nullptr, W, omega, st);
+        launch_vec<float, kVecF32, true>(L, colour, x, beta, nullptr, W, omega, st, Wblack);
 }
 
 void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *rho,
@@ -87,9 +92,12 @@ void launch_sweep_mixed(const Layout &L, int colour, float *delta, const float *
 // sweep reads no per-voxel c/D.
 //
 // Ws <- W r_i r_nb on the interior faces of every red voxel (0 on faces to the
-// boundary), r = sqrt(gamma) of both ends.
+// boundary), r = sqrt(gamma) of both ends; with Wsb, the same values also by
+// black end: face f of red slot q is face f ^ 1 of its black neighbour
+// (Wsb's faces to the ring stay 0 from its allocation).
 __global__ void __launch_bounds__(256) k_scaled_weights(Layout L, const float *__restrict__ W,
                                                         float *__restrict__ Ws,
+                                                        float *__restrict__ Wsb,
                                                         const float *__restrict__ gamma,
                                                         ItemDecode dec, unsigned items)
 {
@@ -113,18 +121,20 @@ __global__ void __launch_bounds__(256) k_scaled_weights(Layout L, const float *_
 #pragma unroll
         for (int f = 0; f < 8; ++f) {
             const long long o = (long long)f * L.S + q;
-            Ws[o] = in[f] ? W[o] * rs * sqrtf(gb[nb[f]]) : 0.0f;
+            const float v = in[f] ? W[o] * rs * sqrtf(gb[nb[f]]) : 0.0f;
+            Ws[o] = v;
+            if (Wsb && in[f]) Wsb[(long long)(f ^ 1) * L.S + nb[f]] = v;
         }
     }
 }
 
-void launch_scaled_weights(const Layout &L, const float *W, float *Ws, const float *gamma,
-                           cudaStream_t st)
+void launch_scaled_weights(const Layout &L, const float *W, float *Ws, float *Wsb,
+                           const float *gamma, cudaStream_t st)
 {
     const long long red_items = item_count(L, L.nchunk) / 2;
     const int blocks = (int)(red_items < kResBlocks ? red_items : kResBlocks);
-    k_scaled_weights<<<blocks, 256, 0, st>>>(L, W, Ws, gamma, make_item_decode(L, L.nchunk),
-                                             (unsigned)red_items);
+    k_scaled_weights<<<blocks, 256, 0, st>>>(L, W, Ws, Wsb, gamma,
+                                             make_item_decode(L, L.nchunk), (unsigned)red_items);
 }
 
 // Deterministic final reduction of the per-block records (one block); with

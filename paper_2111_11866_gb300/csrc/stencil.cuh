@@ -292,9 +292,12 @@ __device__ __forceinline__ void stv(float *p, const float (&v)[N])
 // black voxels, its face weight) comes from the adjacent lane by shuffle when
 // that lane holds the adjacent group of the same row, and is loaded
 // otherwise.  kAllW (red only): also load the weights of faces outside the
-// grid (a red voxel owns them).  All 32 lanes of the warp must call this;
-// lanes without a group pass act = false (fn is not called).
-template <int C, typename WT, int N, bool kAllW, typename Fn>
+// grid (a red voxel owns them).  kOwnW (black only): W is a copy of the
+// weights stored by their black end ([8][S] at the black voxel's own slot,
+// faces to the ring 0), read as the red voxels read theirs.  All 32 lanes of
+// the warp must call this; lanes without a group pass act = false (fn is not
+// called).
+template <int C, typename WT, int N, bool kAllW, typename Fn, bool kOwnW = false>
 __device__ __forceinline__ void gather_core(const Layout &L, const float *__restrict__ x,
                                             const WT *__restrict__ W, bool act, int row, int s0,
                                             const RowPos &rp, Fn fn)
@@ -312,13 +315,16 @@ __device__ __forceinline__ void gather_core(const Layout &L, const float *__rest
     ldv<N>(X, act, xo + q);
     // x-direction weights: red owns faces 0 (-x) and 1 (+x); black reads
     // face 1 of the red voxel on its left and face 0 of the one on its right
+    // (or, with kOwnW, its own faces 0 and 1)
+    constexpr bool kOwn = C == 0 || kOwnW;
     ldv<N>(W0, act, W + 0 * S + q);
     ldv<N>(W1, act, W + 1 * S + q);
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
-        // red: own face f+2; black: the opposite face of the red neighbour
-        const long long wi = C == 0 ? (long long)(f + 2) * S + q
-                                    : (long long)((f + 2) ^ 1) * S + q + off[f];
+        // red (or kOwnW): own face f+2; black: the opposite face of the red
+        // neighbour
+        const long long wi = kOwn ? (long long)(f + 2) * S + q
+                                  : (long long)((f + 2) ^ 1) * S + q + off[f];
         ldv<N>(a[f], (kAllW && C == 0) ? act : in[f], W + wi);
         ldv<N>(y[f], in[f], xo + q + off[f]);
     }
@@ -336,10 +342,10 @@ __device__ __forceinline__ void gather_core(const Layout &L, const float *__rest
     float xl = 0.0f, xr = 0.0f, wl = 0.0f, wr = 0.0f;
     if (e == 0) {
         xl = shL ? xLs : (hasL ? xo[q - 1] : 0.0f);
-        if (C == 1) wl = shL ? wLs : (hasL ? ldw(W + 1 * S + q - 1) : 0.0f);
+        if (!kOwn) wl = shL ? wLs : (hasL ? ldw(W + 1 * S + q - 1) : 0.0f);
     } else {
         xr = shR ? xRs : (hasR ? xo[q + N] : 0.0f);
-        if (C == 1) wr = shR ? wRs : (hasR ? ldw(W + 0 * S + q + N) : 0.0f);
+        if (!kOwn) wr = shR ? wRs : (hasR ? ldw(W + 0 * S + q + N) : 0.0f);
     }
 #pragma unroll
     for (int m = 0; m < N; ++m) {
@@ -347,7 +353,7 @@ __device__ __forceinline__ void gather_core(const Layout &L, const float *__rest
         const float xm = e == 0 ? (m == 0 ? xl : X[m - 1]) : X[m];
         const float xp = e == 0 ? X[m] : (m == N - 1 ? xr : X[m + 1]);
         float wm, wp;
-        if (C == 0) {
+        if (kOwn) {
             wm = W0[m];
             wp = W1[m];
         } else {
@@ -363,23 +369,22 @@ __device__ __forceinline__ void gather_core(const Layout &L, const float *__rest
 // Neighbour sums acc[m] = sum_f w_f x_nb(f) of a group (see gather_core):
 // products rounded, the fixed addition tree of sum8, a face outside the grid
 // contributes exactly 0.
-template <int C, typename WT, int N>
+template <int C, typename WT, int N, bool kOwnW = false>
 __device__ __forceinline__ void gather_vec(const Layout &L, const float *__restrict__ x,
                                            const WT *__restrict__ W, bool act, int row, int s0,
                                            const RowPos &rp, float (&acc)[N])
 {
-    gather_core<C, WT, N, false>(
-        L, x, W, act, row, s0, rp,
-        [&](int m, float xm, float xp, float wm, float wp, bool inm, bool inp,
-            const float (&a)[6][N], const float (&y)[6][N], const bool (&in)[6]) {
-            acc[m] = sum8(inm ? __fmul_rn(wm, xm) : 0.0f, inp ? __fmul_rn(wp, xp) : 0.0f,
-                          in[0] ? __fmul_rn(a[0][m], y[0][m]) : 0.0f,
-                          in[1] ? __fmul_rn(a[1][m], y[1][m]) : 0.0f,
-                          in[2] ? __fmul_rn(a[2][m], y[2][m]) : 0.0f,
-                          in[3] ? __fmul_rn(a[3][m], y[3][m]) : 0.0f,
-                          in[4] ? __fmul_rn(a[4][m], y[4][m]) : 0.0f,
-                          in[5] ? __fmul_rn(a[5][m], y[5][m]) : 0.0f);
-        });
+    auto fn = [&](int m, float xm, float xp, float wm, float wp, bool inm, bool inp,
+                  const float (&a)[6][N], const float (&y)[6][N], const bool (&in)[6]) {
+        acc[m] = sum8(inm ? __fmul_rn(wm, xm) : 0.0f, inp ? __fmul_rn(wp, xp) : 0.0f,
+                      in[0] ? __fmul_rn(a[0][m], y[0][m]) : 0.0f,
+                      in[1] ? __fmul_rn(a[1][m], y[1][m]) : 0.0f,
+                      in[2] ? __fmul_rn(a[2][m], y[2][m]) : 0.0f,
+                      in[3] ? __fmul_rn(a[3][m], y[3][m]) : 0.0f,
+                      in[4] ? __fmul_rn(a[4][m], y[4][m]) : 0.0f,
+                      in[5] ? __fmul_rn(a[5][m], y[5][m]) : 0.0f);
+    };
+    gather_core<C, WT, N, false, decltype(fn), kOwnW>(L, x, W, act, row, s0, rp, fn);
 }
 
 // Exact residual of the step system in flux form for the N voxels of a
@@ -438,9 +443,10 @@ __device__ __forceinline__ void flux_residual_vec(const Layout &L, const float *
 // One colour-C relaxation of the N voxels of a group (see gather_vec):
 // x <- x + omega (B + G acc - x) with B and G the [2][S] per-voxel
 // coefficients, the arithmetic of gather_vec + relax.  kUnit: G = 1 (the
-// symmetrically scaled system, where no G is stored or read).  Slots past the
-// row end (i >= n1) are padding and keep their value (zero).
-template <int C, typename WT, int N, bool kUnit = false>
+// symmetrically scaled system, where no G is stored or read).  kOwnW (black
+// only): W is the copy of the weights by black end (gather_core).  Slots past
+// the row end (i >= n1) are padding and keep their value (zero).
+template <int C, typename WT, int N, bool kUnit = false, bool kOwnW = false>
 __device__ __forceinline__ void relax_vec(const Layout &L, float *__restrict__ x,
                                           const float *__restrict__ B,
                                           const float *__restrict__ Gm,
@@ -459,7 +465,7 @@ __device__ __forceinline__ void relax_vec(const Layout &L, float *__restrict__ x
     } else {
         ldv<N>(Gp, act, Gm + C * S + q);
     }
-    gather_vec<C, WT, N>(L, x, W, act, row, s0, rp, acc);
+    gather_vec<C, WT, N, kOwnW>(L, x, W, act, row, s0, rp, acc);
     if (!act) return;
     const int e = C ^ rp.p;
     float out[N];

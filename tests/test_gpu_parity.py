@@ -309,16 +309,25 @@ SWEEP_DIMS = [(69, 21, 13, 5), (40, 17, 6, 1), (31, 9, 5, 2), (64, 24, 12, 7), (
 def test_ragged_layouts_match_oracle(dims, lean):
     """Rows of one to nine warps' 64 slots with ragged ends, odd y-blocks,
     n4 = 1 and 2, on the full handle (scaled sweeps) and the lean one
-    (unscaled sweeps): two steps against the oracle, per-voxel bound."""
+    (unscaled sweeps): two steps against the oracle, per-voxel bound; both
+    ways of reading the black pass's weights give the same bits."""
     n1, n2, n3, n4 = dims
     image = synth.random_field(sum(dims), dims)
     seeds = [(n1 // 2, n2 // 2, n3 // 2, 0), (n1 // 3, n2 // 3, n3 // 3, n4 - 1)]
-    p = _lib.Params.defaults()
-    p.r_ball = p.R_init = 5.0
-    with _lib.Seg4D(dims, params=p, lean=lean) as s:
-        s.set_image(image)
-        s.set_seeds(seeds)
-        s.step(2)
-        u = s.read_u()
+    out = {}
+    for variant in (1, 2):
+        p = _lib.Params.defaults()
+        p.r_ball = p.R_init = 5.0
+        p.sweep_variant = variant
+        with _lib.Seg4D(dims, params=p, lean=lean) as s:
+            s.set_image(image)
+            s.set_seeds(seeds)
+            info = s.step(2)
+            out[variant] = (s.read_u(), info["sweeps_total"])
+    # the black pass reading the weights by black end (1) or across the faces
+    # (2) gives the same bits and the same sweep counts
+    np.testing.assert_array_equal(out[1][0], out[2][0])
+    assert out[1][1] == out[2][1]
+    u = out[1][0]
     r, _ = O.segment(image.astype(np.float64), seeds, oracle_params(p), nsteps=2)
     assert np.abs(u - r).max() <= REL_TOL * max(np.abs(r).max(), 1e-30)

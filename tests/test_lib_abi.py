@@ -58,9 +58,10 @@ def test_default_params_and_device_bytes(lib):
     assert p.delta == 0.5 and p.vartheta == 0.5 and p.lambda_th == 0.87 and p.R_init == 12.0
     assert abs(p.sigma_t - 0.01**2 / 8) < 1e-20
     nb = _lib.Seg4D.device_bytes((128, 128, 64, 32))
-    # 72 bytes per voxel of grid state (G once per face) plus 32 of the FP32
-    # solve's arrays, and a small side table of boundary-face G
-    assert 100 * 33554432 < nb < 110 * 33554432
+    # 72 bytes per voxel of grid state (G once per face) plus 48 of the FP32
+    # solve's arrays (scaled weights by both ends), and a small side table of
+    # boundary-face G
+    assert 115 * 33554432 < nb < 125 * 33554432
     # the lean handle: 64 bytes per voxel
     nl = _lib.Seg4D.device_bytes((128, 128, 64, 32), lean=True)
     assert 60 * 33554432 < nl < 68 * 33554432
