@@ -749,19 +749,16 @@ struct seg4d_batch {
     // pinned host copies are not rewritten before their last upload has run
     BWin *d_wins = nullptr, *h_wins = nullptr;
     long long *d_chunk = nullptr, *h_chunk = nullptr;   // reduction chunks
-    long long *d_tile = nullptr, *h_tile = nullptr;     // 256-slot tiles
-    long long *d_ptile = nullptr, *h_ptile = nullptr;   // sweep tiles of 256 N-slot groups
     long long *d_seed = nullptr, *h_seed = nullptr;     // seed blocks
     cudaEvent_t ev_table = nullptr;
     bool table_pending = false;
     std::vector<std::pair<int, float *>> table_key;     // (window id, x) uploaded
-    long long n_chunk = 0, n_tile = 0, n_ptile = 0, n_seed = 0;
+    long long n_chunk = 0, n_seed = 0;
     double *d_out = nullptr, *h_out = nullptr;
     double *d_parts = nullptr;
     size_t parts_cap = 0;    // chunk records
     long long launches = 0;
     double sweep_ms = 0.0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
     // solves with device-side checks (batch_solve): per-window state, unit
     // counts, the round tables and their staging, the count of windows still
     // solving read back a few rounds late
@@ -881,34 +878,22 @@ seg4d_status set_table(seg4d_batch *b, const std::vector<Window *> &ws)
         BCK(cudaEventSynchronize(b->ev_table));
         b->table_pending = false;
     }
-    long long c = 0, t = 0, pt = 0, sd = 0;
+    long long c = 0, sd = 0;
     for (size_t i = 0; i < ws.size(); ++i) {
         b->h_wins[i] = ws[i]->d;
         b->h_chunk[i] = c;
-        b->h_tile[i] = t;
-        b->h_ptile[i] = pt;
         b->h_seed[i] = sd;
         c += chunks_of(*ws[i]);
-        t += win_tiles(ws[i]->L);
-        pt += win_gtiles(ws[i]->L, b->p.precision == 1 ? kVecBF16 : kVecF32);
         sd += ws[i]->d.nseeds;
     }
     const size_t n = ws.size();
     b->h_chunk[n] = c;
-    b->h_tile[n] = t;
-    b->h_ptile[n] = pt;
     b->h_seed[n] = sd;
     b->n_chunk = c;
-    b->n_tile = t;
-    b->n_ptile = pt;
     b->n_seed = sd;
     BCK(cudaMemcpyAsync(b->d_wins, b->h_wins, sizeof(BWin) * n, cudaMemcpyHostToDevice, b->stream));
     BCK(cudaMemcpyAsync(b->d_chunk, b->h_chunk, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
                         b->stream));
-    BCK(cudaMemcpyAsync(b->d_tile, b->h_tile, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
-                        b->stream));
-    BCK(cudaMemcpyAsync(b->d_ptile, b->h_ptile, sizeof(long long) * (n + 1),
-                        cudaMemcpyHostToDevice, b->stream));
     BCK(cudaMemcpyAsync(b->d_seed, b->h_seed, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
                         b->stream));
     BCK(cudaEventRecord(b->ev_table, b->stream));
@@ -957,8 +942,6 @@ struct SolveItem {
     int iters;
     bool done;
     bool ok;
-    int next_check;     // sweep count of the window's next stopping test
-    CheckState cs;      // its residual history (check_decision)
 };
 
 // Batched red-black SOR over every window of `items` (each window's d.x,
@@ -1187,8 +1170,7 @@ seg4d_status batch_setup(seg4d_batch *b, std::vector<Window *> &pend, long long 
         if ((st = reduce_windows(b, ws.size()))) return st;
         std::vector<SolveItem> items;
         for (size_t i = 0; i < ws.size(); ++i)
-            items.push_back(SolveItem{ws[i], std::sqrt(b->h_out[4 * i]), 0.0, 0, false, false, 0,
-                                      CheckState{}});
+            items.push_back(SolveItem{ws[i], std::sqrt(b->h_out[4 * i]), 0.0, 0, false, false});
         if ((st = batch_solve(b, items, p.omega_smooth, p.tol_smooth, p.max_iters, p.check_every,
                               sweeps)))
             return st;
@@ -1251,7 +1233,7 @@ seg4d_status batch_step(seg4d_batch *b, std::vector<Window *> &act, long long &s
         items.push_back(SolveItem{act[i], std::sqrt(b->h_out[4 * i]),
                                   std::max(std::fabs(b->h_out[4 * i + 1]),
                                            std::fabs(b->h_out[4 * i + 2])),
-                                  0, false, false, 0, CheckState{}});
+                                  0, false, false});
     if ((st = batch_solve(b, items, p.omega, p.tol, p.max_iters, p.check_every, sweeps, mixed,
                           p.tol_inf, p.omega_adapt != 0)))
         return st;
@@ -1277,20 +1259,14 @@ void batch_free(seg4d_batch *b)
     cudaFree(b->arena_mem);
     cudaFree(b->d_wins);
     cudaFree(b->d_chunk);
-    cudaFree(b->d_tile);
-    cudaFree(b->d_ptile);
     cudaFree(b->d_seed);
     cudaFree(b->d_out);
     cudaFree(b->d_parts);
     if (b->h_wins) cudaFreeHost(b->h_wins);
     if (b->h_chunk) cudaFreeHost(b->h_chunk);
-    if (b->h_tile) cudaFreeHost(b->h_tile);
-    if (b->h_ptile) cudaFreeHost(b->h_ptile);
     if (b->h_seed) cudaFreeHost(b->h_seed);
     if (b->ev_table) cudaEventDestroy(b->ev_table);
     if (b->h_out) cudaFreeHost(b->h_out);
-    if (b->e0) cudaEventDestroy(b->e0);
-    if (b->e1) cudaEventDestroy(b->e1);
     cudaFree(b->d_sw);
     cudaFree(b->d_cnt);
     cudaFree(b->d_tab_int);
@@ -1332,18 +1308,13 @@ seg4d_status seg4d_batch_create(size_t arena_bytes, int max_windows, void *cuda_
     bool ok = cudaMalloc(&b->arena_mem, arena) == cudaSuccess &&
               cudaMalloc(&b->d_wins, sizeof(BWin) * max_windows) == cudaSuccess &&
               cudaMalloc(&b->d_chunk, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
-              cudaMalloc(&b->d_tile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
-              cudaMalloc(&b->d_ptile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMalloc(&b->d_seed, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMalloc(&b->d_out, 4 * sizeof(double) * max_windows) == cudaSuccess &&
               cudaMallocHost(&b->h_wins, sizeof(BWin) * max_windows) == cudaSuccess &&
               cudaMallocHost(&b->h_chunk, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
-              cudaMallocHost(&b->h_tile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
-              cudaMallocHost(&b->h_ptile, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaMallocHost(&b->h_seed, sizeof(long long) * (max_windows + 1)) == cudaSuccess &&
               cudaEventCreate(&b->ev_table) == cudaSuccess &&
-              cudaMallocHost(&b->h_out, 4 * sizeof(double) * max_windows) == cudaSuccess &&
-              cudaEventCreate(&b->e0) == cudaSuccess && cudaEventCreate(&b->e1) == cudaSuccess;
+              cudaMallocHost(&b->h_out, 4 * sizeof(double) * max_windows) == cudaSuccess;
     const size_t mw = (size_t)max_windows;
     ok = ok && cudaMalloc(&b->d_sw, sizeof(BSolve) * mw) == cudaSuccess &&
          cudaMallocHost(&b->h_sw, sizeof(BSolve) * mw) == cudaSuccess &&
